@@ -1,0 +1,47 @@
+"""The transform by direct summation (oracle; test infrastructure only).
+
+Synthesis is the definition f_j = sum_k c_k phi_k(x_j), i.e. f = Phi c (Eq. ``MHT-sum``,
+Sec. 1).  Analysis is the weighted adjoint c = Phi^H diag(w) f, the fast adjoint that maps
+point values to coefficients (Sec. 1); Phi^H is the conjugate transpose (the paper's ``*``).
+With w = None the plain adjoint Phi^H f is returned.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def synthesize(Phi: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """f = Phi c for a dense Phi (n, m) and c (m,) or (m, k)."""
+    return Phi @ c
+
+
+def analyze(Phi: np.ndarray, f: np.ndarray, w: np.ndarray | None = None) -> np.ndarray:
+    """c = Phi^H diag(w) f for a dense Phi (n, m) and f (n,) or (n, k)."""
+    g = f if w is None else (w[:, None] * f if f.ndim == 2 else w * f)
+    return Phi.conj().T @ g
+
+
+def synthesize_rows(row_eval, c: np.ndarray, rows: np.ndarray, chunk: int = 64) -> np.ndarray:
+    """f(rows) = Phi(rows, :) c with Phi evaluated row block by row block (matrix-free).
+
+    ``row_eval(rows) -> (len(rows), m)`` returns rows of Phi.
+    """
+    rows = np.asarray(rows)
+    out = []
+    for s in range(0, len(rows), chunk):
+        out.append(row_eval(rows[s:s + chunk]) @ c)
+    return np.concatenate(out, axis=0)
+
+
+def analyze_columns(col_eval, f: np.ndarray, cols: np.ndarray, w: np.ndarray | None = None,
+                    chunk: int = 64) -> np.ndarray:
+    """c(cols) = Phi(:, cols)^H diag(w) f with Phi evaluated column block by block.
+
+    ``col_eval(cols) -> (n, len(cols))`` returns columns of Phi.
+    """
+    g = f if w is None else (w[:, None] * f if f.ndim == 2 else w * f)
+    cols = np.asarray(cols)
+    out = []
+    for s in range(0, len(cols), chunk):
+        out.append(col_eval(cols[s:s + chunk]).conj().T @ g)
+    return np.concatenate(out, axis=0)
