@@ -1,0 +1,272 @@
+/*
+ * mht.h -- C ABI of the butterfly-accelerated manifold harmonic transform (BF-MHT).
+ *
+ * The transform (Sec. 1, Eq. MHT-sum): given n points x_j on a manifold and the first m
+ * Laplace-Beltrami eigenfunctions phi_k, Phi is the n x m matrix Phi_jk = phi_k(x_j), and
+ *     synthesis   f = Phi c                    (mht_synthesize)
+ *     analysis    c = Phi^H diag(w) f          (mht_analyze; the fast adjoint of Sec. 1,
+ *                                               Phi^H the conjugate transpose, w >= 0)
+ * are applied through a row-wise butterfly factorization of Phi (Sec. 2, Algorithm 1;
+ * streaming post-order build of Sec. 4, Algorithm 3) with a Fiedler space tree (Sec. 3,
+ * Algorithm 2) and an eigenvalue-ordered frequency tree.  The factorization is built in
+ * FP64 on the host; the apply runs as CUDA kernels on the caller's stream.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MHT_OK or an error code; on error mht_last_error() returns a message
+ *    (thread-local, valid until the next call on the same thread).  No exception crosses
+ *    the ABI.  A failed apply leaves its outputs unspecified.
+ *  - Element types.  A plan has a field (real/complex) and an apply mode:
+ *      MHT_APPLY_FP64  -> vectors are double (real) or interleaved (re, im) double pairs;
+ *      MHT_APPLY_FP32 / MHT_APPLY_3XTF32 -> float or interleaved float pairs.
+ *  - Vector layout: column-major.  c is m x nrhs with leading dimension ldc >= m (counted
+ *    in elements, one complex value = one element); f is n x nrhs with ldf >= n.  Rows are
+ *    in the caller's ORIGINAL point / mode order (the order the problem was given in).
+ *  - Device memory is owned by the caller.  The library never allocates device memory:
+ *    the caller queries sizes (mht_plan_device_bytes), allocates, and binds the buffers
+ *    (mht_plan_bind_device).  Host memory of a plan is owned by the plan.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device applies are asynchronous; input and output buffers must not alias and must stay
+ *    valid until the stream reaches the end of the call.  Two applies on one plan must not
+ *    run concurrently (they share the plan's bound workspace).
+ */
+#ifndef MHT_H
+#define MHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mht_plan mht_plan;
+
+typedef enum {
+  MHT_OK = 0,
+  MHT_ERR_INVALID_ARG = 1, /* a NULL, size, stride or enum argument is out of range   */
+  MHT_ERR_OOM = 2,         /* host allocation failed, or a caller buffer is too small */
+  MHT_ERR_CALLBACK = 3,    /* the user's Phi evaluator returned non-zero              */
+  MHT_ERR_NUMERIC = 4,     /* NaN/Inf met while building the factorization            */
+  MHT_ERR_CUDA = 5,        /* a CUDA runtime call failed (message has the CUDA error) */
+  MHT_ERR_FORMAT = 6,      /* plan file or imported factors are malformed             */
+  MHT_ERR_TIMEOUT = 7,     /* a bounded device wait ran out (persistent batched apply)*/
+  MHT_ERR_UNSUPPORTED = 8, /* valid request this build does not implement             */
+  MHT_ERR_NOT_BOUND = 9    /* apply called before mht_plan_bind_device                */
+} mht_status;
+
+typedef enum { MHT_REAL = 0, MHT_COMPLEX = 1 } mht_field;
+
+typedef enum {
+  MHT_APPLY_FP64 = 0,  /* factors and vectors in double, FP64 arithmetic                */
+  MHT_APPLY_FP32 = 1,  /* factors and vectors in float, FP32 SIMT arithmetic            */
+  MHT_APPLY_3XTF32 = 2 /* float data; multi-RHS block products split into three TF32
+                          tensor-core products with FP32 accumulation (hi*hi + hi*lo +
+                          lo*hi); single-RHS applies use the FP32 kernels              */
+} mht_apply_mode;
+
+typedef enum {
+  MHT_TREE_AUTO = 0,        /* RECT for MHT_EVAL_TORUS, FIEDLER otherwise              */
+  MHT_TREE_FIEDLER = 1,     /* Algorithm 2, mesh-free rule: sign of phi_2 of a kNN
+                               heat-kernel graph Laplacian on each node's points      */
+  MHT_TREE_RECT = 2,        /* flat periodic square: exact Neumann Fiedler function of
+                               each node's rectangle (midpoint cut of the longer side;
+                               sin(x1) at the periodic root)                          */
+  MHT_TREE_PCA_MEDIAN = 3,  /* median split along the principal axis (equal sizes)     */
+  MHT_TREE_GIVEN = 4        /* problem->space_perm / space_offsets are used as is      */
+} mht_tree_kind;
+
+typedef enum {
+  MHT_EVAL_CALLBACK = 0, /* problem->eval(ctx, rows, nrows, cols, ncols, out)           */
+  MHT_EVAL_TORUS = 1,    /* Phi_jk = exp(i k_k . x_j), Eq. 2D-DFT; points (n x 2),
+                            problem->torus_modes (m x 2 int64); field must be COMPLEX   */
+  MHT_EVAL_SPHERE = 2,   /* orthonormal real spherical harmonics, column k = l^2+l+mm,
+                            cos(mm lon) for mm > 0, sin(|mm| lon) for mm < 0, no
+                            Condon-Shortley phase; points (n x 3); field must be REAL    */
+  MHT_EVAL_DENSE = 3     /* problem->dense: column-major n x m FP64 (interleaved pairs if
+                            complex) with leading dimension ld_dense >= n               */
+} mht_eval_kind;
+
+/* Entries of Phi in FP64 for original indices rows[0..nrows) x cols[0..ncols), written
+ * column-major to out[nrows * ncols] (interleaved (re, im) pairs if complex).  Called
+ * concurrently from several host threads.  Return 0 on success, non-zero to abort the
+ * build with MHT_ERR_CALLBACK. */
+typedef int (*mht_eval_fn)(void* ctx, const int64_t* rows, int64_t nrows,
+                           const int64_t* cols, int64_t ncols, double* out);
+
+typedef struct {
+  int64_t n, m;                 /* points (rows of Phi) and modes (columns)            */
+  mht_field field;
+  const double* eigenvalues;    /* [m] defines the frequency order (stable sort)       */
+  mht_eval_kind eval_kind;
+  mht_eval_fn eval;             /* MHT_EVAL_CALLBACK                                   */
+  void* eval_ctx;
+  const double* points;         /* [n * dim] row-major; trees and built-in evaluators  */
+  int32_t dim;
+  const int64_t* torus_modes;   /* [m * 2] for MHT_EVAL_TORUS                          */
+  const double* dense;          /* MHT_EVAL_DENSE                                      */
+  int64_t ld_dense;
+  const int64_t* space_perm;    /* MHT_TREE_GIVEN: [n] tree order -> original point    */
+  const int64_t* space_offsets; /* MHT_TREE_GIVEN: [2^L + 1] leaf ranges, depth L      */
+  const double* weights;        /* [n] quadrature / mass weights w for analysis; NULL = 1 */
+} mht_problem;
+
+typedef struct {
+  double eps;          /* ID tolerance: rank = #{k : |R_kk| > eps |R_11|}              */
+  int64_t leaf_size;   /* L = max(0, ceil(log2(n / leaf_size))) unless levels >= 0      */
+  int32_t levels;      /* < 0: derive L from leaf_size                                */
+  mht_apply_mode mode;
+  mht_tree_kind tree;
+  uint64_t seed;       /* row sampling and Lanczos start vectors                       */
+  int32_t num_threads; /* host threads for the build; 0 = OpenMP default               */
+  double oversample;   /* row-sampled IDs use min(|tau|, ceil(oversample * K) + 16) rows;
+                          <= 0 disables sampling (exact IDs on all rows)                */
+} mht_options;
+
+/* Factors as plain arrays: the content of a factorization, in the notation of Sec. 2.
+ * Blocks at level l (0..L) are numbered b = tau * 2^(L-l) + nu (tau at depth l of the
+ * space tree, nu at height l of the frequency tree).  Block b has rank r = ranks[l*2^L+b]
+ * and input size K (level 0: |nu|; level l >= 1: ranks of blocks (p, 2nu) and (p, 2nu+1)
+ * at level l-1 added, p = tau / 2).  local_perm lists K local input indices with the r
+ * skeleton indices first; transfer holds T~ (r x (K-r), row-major), so that the block's
+ * interpolation matrix is [I | T~] P^T.  column_bases holds U_tau = Phi(tau, J_tau) for each
+ * space leaf tau (|tau| x r_L row-major, rows in tree order).  All arrays are concatenated
+ * level by level, block by block.  Complex values are interleaved (re, im) pairs. */
+typedef struct {
+  int64_t n, m;
+  int32_t levels;
+  mht_field field;
+  int64_t* space_perm;     /* [n] tree-order position -> original point index          */
+  int64_t* space_offsets;  /* [2^L + 1]                                                */
+  int64_t* mode_perm;      /* [m] frequency-order position -> original mode index      */
+  int64_t* mode_offsets;   /* [2^L + 1]                                                */
+  int32_t* ranks;          /* [(L + 1) * 2^L]                                          */
+  int32_t* local_perm;     /* [sum of K over all blocks]                               */
+  double* transfer;        /* [sum of r (K - r)] (x2 if complex)                       */
+  double* column_bases;    /* [sum of |tau| r_L] (x2 if complex)                       */
+  double* weights;         /* [n] or NULL (import only)                                */
+} mht_factors;
+
+typedef struct {
+  int64_t n, m;
+  int32_t levels;
+  mht_field field;
+  mht_apply_mode mode;
+  double eps;
+  int64_t blocks_per_level;     /* 2^L                                                  */
+  int64_t local_perm_entries;   /* sizes of the mht_factors arrays                      */
+  int64_t transfer_entries;     /* complex entries count once                           */
+  int64_t column_basis_entries;
+  int64_t stored_entries;       /* transfer + column-basis entries (the applied data)   */
+  int64_t max_rank;
+  int64_t workspace_entries_per_rhs;
+  size_t factor_bytes;          /* device bytes of the packed factors                   */
+  size_t algorithmic_bytes;     /* bytes one single-RHS apply must move: stored entries,
+                                   index lists, descriptors, c and f (see the design notes) */
+  double build_seconds;
+} mht_plan_info_t;
+
+typedef struct {
+  int64_t rank_min, rank_median, rank_max, rank_sum;
+  int64_t transfer_entries;     /* T~ entries at this level (level L+1: column bases)   */
+  size_t bytes;                 /* packed device bytes of this stage's factors          */
+  size_t algorithmic_bytes;     /* bytes one single-RHS launch of this stage must move:
+                                   stored matrix entries, index lists, descriptors, the
+                                   input entries it gathers and the outputs it writes   */
+} mht_level_info_t;
+
+/* ---- build, import, export -------------------------------------------------------- */
+
+/* Builds the butterfly factorization of Phi (Algorithms 1-3) in FP64 on the host and packs
+ * it for the device.  *out receives a new plan owned by the caller (free with
+ * mht_destroy).  Errors: INVALID_ARG (sizes, enums, missing evaluator data), CALLBACK,
+ * NUMERIC, OOM. */
+mht_status mht_build_plan(const mht_problem* problem, const mht_options* options,
+                          mht_plan** out);
+
+/* Creates a plan from explicit factors (layout above); the arrays are copied and may be
+ * freed after the call.  options->mode selects the apply precision; other option fields
+ * are ignored.  Errors: INVALID_ARG, FORMAT (inconsistent ranks, permutations, offsets). */
+mht_status mht_plan_import(const mht_factors* factors, const mht_options* options,
+                           mht_plan** out);
+
+/* Copies the plan's FP64 factors into caller arrays sized from mht_plan_info (scalar
+ * fields of *factors are filled in; array pointers may be NULL to skip an array). */
+mht_status mht_plan_export(const mht_plan* plan, mht_factors* factors);
+
+mht_status mht_plan_info(const mht_plan* plan, mht_plan_info_t* info);
+
+/* level in 0..L for transfer levels, L+1 for the column bases U. */
+mht_status mht_plan_level_info(const mht_plan* plan, int32_t level, mht_level_info_t* info);
+
+/* ---- device binding ------------------------------------------------------------------ */
+
+/* Device bytes the caller must provide: the packed factors (fixed) and a workspace that
+ * serves applies with up to max_nrhs right-hand sides (intermediate butterfly vectors and
+ * host-transfer staging).  Both buffers need 256-byte alignment. */
+mht_status mht_plan_device_bytes(const mht_plan* plan, int64_t max_nrhs,
+                                 size_t* factor_bytes, size_t* workspace_bytes);
+
+/* Uploads the packed factors into factor_dev (cudaMemcpyAsync on `stream`, complete when
+ * the call returns) and records both buffers in the plan.  The buffers stay owned by the
+ * caller and must outlive the plan's use.  Re-binding replaces the previous binding.
+ * Errors: INVALID_ARG (NULL, misaligned, too small), CUDA. */
+mht_status mht_plan_bind_device(mht_plan* plan, void* factor_dev, size_t factor_bytes,
+                                void* workspace_dev, size_t workspace_bytes,
+                                int64_t max_nrhs, void* stream);
+
+/* ---- applies ------------------------------------------------------------------------- */
+
+/* f = Phi c (synthesis, Eq. MHT-sum): leaf stage V, transfer levels l = 1..L, column
+ * bases U, each a CUDA kernel launch on `stream`.  c_dev: m x nrhs, f_dev: n x nrhs device
+ * arrays in the plan's element type.  1 <= nrhs <= the bound max_nrhs. */
+mht_status mht_synthesize(mht_plan* plan, const void* c_dev, int64_t ldc, void* f_dev,
+                          int64_t ldf, int64_t nrhs, void* stream);
+
+/* f = diag(w) Phi c: synthesis followed by the analysis weights (the adjoint of weighted
+ * analysis, used for its gradient).  Same layout rules as mht_synthesize. */
+mht_status mht_synthesize_weighted(mht_plan* plan, const void* c_dev, int64_t ldc, void* f_dev,
+                                   int64_t ldf, int64_t nrhs, void* stream);
+
+/* c = Phi^H diag(w) f if weighted (w from the problem or factors; all ones if none was
+ * given), else c = Phi^H f: the transposed sweep U^H, R^H for l = L..1, V^H (leaves last),
+ * gather form without atomics.  Same layout rules as mht_synthesize. */
+mht_status mht_analyze(mht_plan* plan, const void* f_dev, int64_t ldf, void* c_dev,
+                       int64_t ldc, int64_t nrhs, int32_t weighted, void* stream);
+
+/* The same transforms on HOST arrays: the input is copied to device staging inside the
+ * bound workspace, the transform runs, and the result is copied back; the call returns
+ * after the stream has finished.  Host arrays should be pinned for full copy speed. */
+mht_status mht_synthesize_host(mht_plan* plan, const void* c_host, int64_t ldc, void* f_host,
+                               int64_t ldf, int64_t nrhs, void* stream);
+mht_status mht_analyze_host(mht_plan* plan, const void* f_host, int64_t ldf, void* c_host,
+                            int64_t ldc, int64_t nrhs, int32_t weighted, void* stream);
+
+/* Number of kernel launches one mht_synthesize / mht_analyze call makes for nrhs. */
+mht_status mht_apply_launch_count(const mht_plan* plan, int64_t nrhs, int64_t* launches);
+
+/* Stage timing for benchmarks.  While enabled, every apply on the plan records a CUDA
+ * event before and after each stage's kernel launch (on the apply's stream).
+ * mht_plan_stage_times waits for the recorded events, returns the summed milliseconds and
+ * launch counts per stage (arrays of L+2 entries: ID levels 0..L, then the column bases)
+ * for direction 0 (synthesis) or 1 (analysis), and clears the record.  Enabling costs one
+ * event record per launch; disabled (the default) it costs nothing. */
+mht_status mht_plan_profile(mht_plan* plan, int32_t enable);
+mht_status mht_plan_stage_times(mht_plan* plan, int32_t direction, double* ms, int64_t* launches);
+
+/* ---- persistence and lifetime -------------------------------------------------------- */
+
+/* Versioned binary plan file with an FNV-1a 64-bit checksum over the payload; the plan
+ * file is the checkpoint of an expensive build.  Load errors: FORMAT, OOM, INVALID_ARG. */
+mht_status mht_plan_save(const mht_plan* plan, const char* path);
+mht_status mht_plan_load(const char* path, const mht_options* options, mht_plan** out);
+
+/* Frees the plan's host memory (device buffers stay with the caller).  NULL is a no-op. */
+mht_status mht_destroy(mht_plan* plan);
+
+const char* mht_last_error(void);
+const char* mht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHT_H */

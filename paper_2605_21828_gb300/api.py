@@ -1,0 +1,372 @@
+"""Python interface to libmht: plans, device binding, transforms and autograd.
+
+Thin marshalling over the C ABI (include/mht.h): every transform runs in the library's CUDA
+kernels; PyTorch supplies device memory, the current stream and autograd.  There is no CPU
+fallback: without the built library or a CUDA device the calls raise.
+
+    plan = Plan.build(n=n, m=m, eigenvalues=lam, evaluator="sphere", points=X,
+                      eps=1e-6, leaf_size=128, mode="fp32", weights=w)
+    plan.bind(max_nrhs=64)
+    f = synthesize(plan, c)            # f = Phi c          (differentiable)
+    c2 = analyze(plan, f)              # c = Phi^H diag(w) f (differentiable)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+_MODES = {"fp64": L.APPLY_FP64, "fp32": L.APPLY_FP32, "3xtf32": L.APPLY_3XTF32}
+_TREES = {"auto": L.TREE_AUTO, "fiedler": L.TREE_FIEDLER, "rect": L.TREE_RECT,
+          "pca": L.TREE_PCA_MEDIAN, "given": L.TREE_GIVEN}
+_EVALS = {"torus": L.EVAL_TORUS, "sphere": L.EVAL_SPHERE, "dense": L.EVAL_DENSE}
+
+
+def _dptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _options(eps=1e-6, leaf_size=128, levels=-1, mode="fp32", tree="auto", seed=0,
+             num_threads=0, oversample=2.0):
+    return L.Options(eps, leaf_size, levels, _MODES[mode], _TREES[tree], seed, num_threads,
+                     oversample)
+
+
+class Plan:
+    """A built (or imported) butterfly factorization and, once bound, its device copy."""
+
+    def __init__(self, handle: C.c_void_p, mode: str, keep=()):
+        self._h = handle
+        self.mode = mode
+        self._keep = list(keep)
+        self._dev = None
+        info = self.info()
+        self.n, self.m, self.levels = info["n"], info["m"], info["levels"]
+        self.complex = bool(info["field"] == L.COMPLEX)
+
+    # ---------------------------------------------------------------- construction
+    @staticmethod
+    def build(*, n, m, eigenvalues, evaluator="sphere", points=None, torus_modes=None,
+              dense=None, callback=None, complex_=None, weights=None, space=None, **opts) -> "Plan":
+        """Builds the factorization on the host (FP64) through ``mht_build_plan``.
+
+        evaluator: "sphere" | "torus" | "dense" | "callback" (then ``callback(rows, cols)``
+        returns Phi(rows, cols) as a float64/complex128 array).  ``space`` = (perm, offsets)
+        selects tree="given".
+        """
+        lib = L.load()
+        lam = np.ascontiguousarray(eigenvalues, dtype=np.float64)
+        keep = [lam]
+        if complex_ is None:
+            complex_ = evaluator == "torus" or (dense is not None and np.iscomplexobj(dense))
+        prob = L.Problem()
+        prob.n, prob.m = n, m
+        prob.field = L.COMPLEX if complex_ else L.REAL
+        prob.eigenvalues = _dptr(lam, C.c_double)
+        if points is not None:
+            pts = np.ascontiguousarray(points, dtype=np.float64)
+            keep.append(pts)
+            prob.points = _dptr(pts, C.c_double)
+            prob.dim = pts.shape[1]
+        if evaluator == "callback":
+            prob.eval_kind = L.EVAL_CALLBACK
+
+            def _cb(ctx, rows, nr, cols, nc, out):
+                try:
+                    r = np.ctypeslib.as_array(rows, (nr,)).copy()
+                    cc = np.ctypeslib.as_array(cols, (nc,)).copy()
+                    blk = np.asarray(callback(r, cc))
+                    o = np.ctypeslib.as_array(out, (nr * nc * (2 if complex_ else 1),))
+                    if complex_:  # column-major, interleaved (re, im)
+                        o[:] = np.ascontiguousarray(blk.astype(np.complex128).T).view(np.float64).reshape(-1)
+                    else:
+                        o[:] = np.asarray(blk, dtype=np.float64).T.reshape(-1)
+                    return 0
+                except Exception:  # noqa: BLE001 - reported to the library as a failure
+                    return 1
+
+            fn = L.EVAL_FN(_cb)
+            keep.append(fn)
+            prob.eval = fn
+        else:
+            prob.eval_kind = _EVALS[evaluator]
+        if torus_modes is not None:
+            km = np.ascontiguousarray(torus_modes, dtype=np.int64)
+            keep.append(km)
+            prob.torus_modes = _dptr(km, C.c_int64)
+        if dense is not None:
+            if complex_:
+                D = np.asfortranarray(dense, dtype=np.complex128)
+                flat = D.reshape(-1, order="F").view(np.float64)
+            else:
+                D = np.asfortranarray(dense, dtype=np.float64)
+                flat = D.reshape(-1, order="F")
+            keep += [D, flat]
+            prob.dense = _dptr(flat, C.c_double)
+            prob.ld_dense = n
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.float64)
+            keep.append(w)
+            prob.weights = _dptr(w, C.c_double)
+        if space is not None:
+            sp = np.ascontiguousarray(space[0], dtype=np.int64)
+            so = np.ascontiguousarray(space[1], dtype=np.int64)
+            keep += [sp, so]
+            prob.space_perm = _dptr(sp, C.c_int64)
+            prob.space_offsets = _dptr(so, C.c_int64)
+            opts["tree"] = "given"
+        o = _options(**opts)
+        h = C.c_void_p()
+        L.check(lib.mht_build_plan(C.byref(prob), C.byref(o), C.byref(h)))
+        return Plan(h, opts.get("mode", "fp32"))
+
+    @staticmethod
+    def from_factors(F: dict, mode: str = "fp32", weights=None) -> "Plan":
+        """Imports explicit factors (dict with the mht_factors arrays) via ``mht_plan_import``."""
+        lib = L.load()
+        cplx = bool(F["complex"])
+        arr = {
+            "space_perm": np.ascontiguousarray(F["space_perm"], dtype=np.int64),
+            "space_offsets": np.ascontiguousarray(F["space_offsets"], dtype=np.int64),
+            "mode_perm": np.ascontiguousarray(F["mode_perm"], dtype=np.int64),
+            "mode_offsets": np.ascontiguousarray(F["mode_offsets"], dtype=np.int64),
+            "ranks": np.ascontiguousarray(F["ranks"], dtype=np.int32),
+            "local_perm": np.ascontiguousarray(F["local_perm"], dtype=np.int32),
+        }
+        for key in ("transfer", "column_bases"):
+            v = np.asarray(F[key])
+            v = np.ascontiguousarray(v, dtype=np.complex128).view(np.float64) if cplx else \
+                np.ascontiguousarray(v, dtype=np.float64)
+            arr[key] = v if v.size else np.zeros(1)
+        fa = L.Factors()
+        fa.n, fa.m, fa.levels = int(F["n"]), int(F["m"]), int(F["levels"])
+        fa.field = L.COMPLEX if cplx else L.REAL
+        for k in ("space_perm", "space_offsets", "mode_perm", "mode_offsets"):
+            setattr(fa, k, _dptr(arr[k], C.c_int64))
+        fa.ranks = _dptr(arr["ranks"], C.c_int32)
+        fa.local_perm = _dptr(arr["local_perm"], C.c_int32) if arr["local_perm"].size else \
+            _dptr(np.zeros(1, np.int32), C.c_int32)
+        fa.transfer = _dptr(arr["transfer"], C.c_double)
+        fa.column_bases = _dptr(arr["column_bases"], C.c_double)
+        if weights is not None:
+            arr["weights"] = np.ascontiguousarray(weights, dtype=np.float64)
+            fa.weights = _dptr(arr["weights"], C.c_double)
+        h = C.c_void_p()
+        L.check(lib.mht_plan_import(C.byref(fa), C.byref(_options(mode=mode)), C.byref(h)))
+        return Plan(h, mode)
+
+    @staticmethod
+    def load(path: str, mode: str = "fp32") -> "Plan":
+        h = C.c_void_p()
+        L.check(L.load().mht_plan_load(path.encode(), C.byref(_options(mode=mode)), C.byref(h)))
+        return Plan(h, mode)
+
+    def save(self, path: str):
+        L.check(L.load().mht_plan_save(self._h, path.encode()))
+
+    def export(self) -> dict:
+        """FP64 factors as numpy arrays (the mht_factors content)."""
+        info = self.info()
+        nb = info["blocks_per_level"]
+        cplx = info["field"] == L.COMPLEX
+        W = 2 if cplx else 1
+        out = {
+            "n": info["n"], "m": info["m"], "levels": info["levels"], "complex": cplx,
+            "space_perm": np.zeros(info["n"], np.int64), "space_offsets": np.zeros(nb + 1, np.int64),
+            "mode_perm": np.zeros(info["m"], np.int64), "mode_offsets": np.zeros(nb + 1, np.int64),
+            "ranks": np.zeros((info["levels"] + 1) * nb, np.int32),
+            "local_perm": np.zeros(max(info["local_perm_entries"], 1), np.int32),
+            "transfer": np.zeros(max(info["transfer_entries"] * W, 1)),
+            "column_bases": np.zeros(max(info["column_basis_entries"] * W, 1)),
+        }
+        fa = L.Factors()
+        for k in ("space_perm", "space_offsets", "mode_perm", "mode_offsets"):
+            setattr(fa, k, _dptr(out[k], C.c_int64))
+        fa.ranks = _dptr(out["ranks"], C.c_int32)
+        fa.local_perm = _dptr(out["local_perm"], C.c_int32)
+        fa.transfer = _dptr(out["transfer"], C.c_double)
+        fa.column_bases = _dptr(out["column_bases"], C.c_double)
+        L.check(L.load().mht_plan_export(self._h, C.byref(fa)))
+        out["local_perm"] = out["local_perm"][:info["local_perm_entries"]]
+        t = out["transfer"][:info["transfer_entries"] * W]
+        u = out["column_bases"][:info["column_basis_entries"] * W]
+        out["transfer"] = t.view(np.complex128) if cplx else t
+        out["column_bases"] = u.view(np.complex128) if cplx else u
+        return out
+
+    def info(self) -> dict:
+        i = L.PlanInfo()
+        L.check(L.load().mht_plan_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in L.PlanInfo._fields_}
+
+    def level_info(self, level: int) -> dict:
+        i = L.LevelInfo()
+        L.check(L.load().mht_plan_level_info(self._h, level, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in L.LevelInfo._fields_}
+
+    def launch_count(self, nrhs: int = 1) -> int:
+        v = C.c_int64()
+        L.check(L.load().mht_apply_launch_count(self._h, nrhs, C.byref(v)))
+        return int(v.value)
+
+    def profile(self, enable: bool = True):
+        L.check(L.load().mht_plan_profile(self._h, 1 if enable else 0))
+
+    def stage_times(self, direction: int):
+        """(ms[L+2], launches[L+2]) summed since the last read (direction 0 synth, 1 analyze)."""
+        ns = self.levels + 2
+        ms = (C.c_double * ns)()
+        ln = (C.c_int64 * ns)()
+        L.check(L.load().mht_plan_stage_times(self._h, direction, ms, ln))
+        return np.array(ms[:]), np.array(ln[:])
+
+    def close(self):
+        if self._h:
+            L.load().mht_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    # ---------------------------------------------------------------- device
+    @property
+    def dtype(self):
+        import torch
+        if self.mode == "fp64":
+            return torch.complex128 if self.complex else torch.float64
+        return torch.complex64 if self.complex else torch.float32
+
+    def device_bytes(self, max_nrhs: int = 1):
+        fb, wb = C.c_size_t(), C.c_size_t()
+        L.check(L.load().mht_plan_device_bytes(self._h, max_nrhs, C.byref(fb), C.byref(wb)))
+        return int(fb.value), int(wb.value)
+
+    def bind(self, device="cuda", max_nrhs: int = 1, factor_buffer=None, workspace_buffer=None):
+        """Allocates (or takes) device buffers and uploads the packed factors."""
+        import torch
+        fb, wb = self.device_bytes(max_nrhs)
+        fac = factor_buffer if factor_buffer is not None else torch.empty(fb + 256, dtype=torch.uint8, device=device)
+        ws = workspace_buffer if workspace_buffer is not None else torch.empty(wb + 256, dtype=torch.uint8, device=device)
+        fp = (fac.data_ptr() + 255) // 256 * 256
+        wp = (ws.data_ptr() + 255) // 256 * 256
+        stream = torch.cuda.current_stream(fac.device).cuda_stream
+        L.check(L.load().mht_plan_bind_device(self._h, C.c_void_p(fp), fb, C.c_void_p(wp), wb, max_nrhs,
+                                              C.c_void_p(stream)))
+        self._dev = (fac, ws, max_nrhs)
+        return self
+
+    @property
+    def max_nrhs(self):
+        return self._dev[2] if self._dev else 0
+
+    def _colmajor(self, x, rows):
+        import torch
+        if x.dtype != self.dtype:
+            raise TypeError(f"expected {self.dtype}, got {x.dtype}")
+        if not x.is_cuda:
+            raise ValueError("device transforms need CUDA tensors (use *_host for host arrays)")
+        if x.shape[0] != rows:
+            raise ValueError(f"expected {rows} rows, got {x.shape[0]}")
+        if x.dim() == 1:
+            return x.contiguous(), 1, True
+        return x.t().contiguous(), x.shape[1], False  # (k, rows) C-order = column-major
+
+    def _apply(self, x, synth: bool, weighted: bool):
+        import torch
+        lib = L.load()
+        nin, nout = (self.m, self.n) if synth else (self.n, self.m)
+        buf, k, vec = self._colmajor(x, nin)
+        out = torch.empty((k, nout), dtype=self.dtype, device=x.device)
+        stream = C.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+        if synth:
+            fn = lib.mht_synthesize_weighted if weighted else lib.mht_synthesize
+            L.check(fn(self._h, C.c_void_p(buf.data_ptr()), nin, C.c_void_p(out.data_ptr()), nout, k, stream))
+        else:
+            L.check(lib.mht_analyze(self._h, C.c_void_p(buf.data_ptr()), nin, C.c_void_p(out.data_ptr()), nout, k,
+                                    1 if weighted else 0, stream))
+        return out[0] if vec else out.t()
+
+    def synthesize_raw(self, c, weighted: bool = False):
+        return self._apply(c, True, weighted)
+
+    def analyze_raw(self, f, weighted: bool = True):
+        return self._apply(f, False, weighted)
+
+    # ---------------------------------------------------------------- host arrays
+    def _host(self, x: np.ndarray, synth: bool, weighted: bool, stream=None):
+        lib = L.load()
+        npdt = {("fp64", False): np.float64, ("fp64", True): np.complex128}.get(
+            (self.mode, self.complex), np.complex64 if self.complex else np.float32)
+        nin, nout = (self.m, self.n) if synth else (self.n, self.m)
+        vec = x.ndim == 1
+        xin = np.asfortranarray(x.reshape(nin, -1), dtype=npdt)
+        k = xin.shape[1]
+        out = np.zeros((nout, k), dtype=npdt, order="F")
+        s = C.c_void_p(stream or 0)
+        if synth:
+            L.check(lib.mht_synthesize_host(self._h, xin.ctypes.data_as(C.c_void_p), nin,
+                                            out.ctypes.data_as(C.c_void_p), nout, k, s))
+        else:
+            L.check(lib.mht_analyze_host(self._h, xin.ctypes.data_as(C.c_void_p), nin,
+                                         out.ctypes.data_as(C.c_void_p), nout, k, 1 if weighted else 0, s))
+        return out[:, 0] if vec else out
+
+    def synthesize_host(self, c: np.ndarray, stream=None) -> np.ndarray:
+        return self._host(c, True, False, stream)
+
+    def analyze_host(self, f: np.ndarray, weighted: bool = True, stream=None) -> np.ndarray:
+        return self._host(f, False, weighted, stream)
+
+
+def _autograd():
+    import torch
+
+    class Synthesize(torch.autograd.Function):
+        """f = Phi c; the gradient is the unweighted adjoint sweep grad_c = Phi^H grad_f."""
+
+        @staticmethod
+        def forward(ctx, c, plan):
+            ctx.plan = plan
+            return plan.synthesize_raw(c)
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.plan.analyze_raw(g.contiguous() if g.dim() == 1 else g, weighted=False), None
+
+    class Analyze(torch.autograd.Function):
+        """c = Phi^H diag(w) f; the gradient is grad_f = diag(w) Phi grad_c."""
+
+        @staticmethod
+        def forward(ctx, f, plan, weighted):
+            ctx.plan, ctx.weighted = plan, weighted
+            return plan.analyze_raw(f, weighted)
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.plan.synthesize_raw(g, weighted=ctx.weighted), None, None
+
+    return Synthesize, Analyze
+
+
+_AG = None
+
+
+def synthesize(plan: Plan, c):
+    """Differentiable f = Phi c on the plan's device."""
+    global _AG
+    if _AG is None:
+        _AG = _autograd()
+    return _AG[0].apply(c, plan)
+
+
+def analyze(plan: Plan, f, weighted: bool = True):
+    """Differentiable c = Phi^H diag(w) f (w = the plan's weights; ones if none)."""
+    global _AG
+    if _AG is None:
+        _AG = _autograd()
+    return _AG[1].apply(f, plan, weighted)

@@ -1,0 +1,146 @@
+// Host-side internals of the BF-MHT library: factorization storage, evaluators, trees,
+// interpolative decompositions, packing and the device-apply interface.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../../include/mht.h"
+#include "../layout.h"
+
+namespace mht {
+
+struct Error : std::runtime_error {
+  mht_status code;
+  Error(mht_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+[[noreturn]] inline void fail(mht_status c, const std::string& m) { throw Error(c, m); }
+
+// One interpolative decomposition block of Sec. 2: input of size K, rank r, local input
+// indices `perm` (skeleton first) and T~ (r x (K - r), row-major; complex interleaved).
+struct Block {
+  int32_t r = 0, K = 0;
+  std::vector<int32_t> perm;
+  std::vector<double> T;
+};
+
+// The butterfly factorization in FP64 (the content of mht_factors).
+struct Factorization {
+  int64_t n = 0, m = 0;
+  int L = 0;
+  bool cplx = false;
+  std::vector<int64_t> space_perm, space_off, mode_perm, mode_off;
+  std::vector<std::vector<Block>> lv;  // [L+1][2^L], block b = tau * 2^(L-l) + nu
+  std::vector<std::vector<double>> U;  // [2^L], |tau| x r_L row-major
+  std::vector<double> weights;         // [n] or empty (= ones)
+
+  int64_t nblk() const { return int64_t(1) << L; }
+  int64_t leaf_rows(int64_t tau) const { return space_off[tau + 1] - space_off[tau]; }
+  // Input size K of block b at level l (level 0: |nu|; else r(p,2nu) + r(p,2nu+1)).
+  int64_t input_size(int l, int64_t b) const;
+  // Offset of the pair (p, 2nu), (p, 2nu+1) at level l-1 read by block b of level l.
+  int64_t pair_index(int l, int64_t b) const {
+    int64_t nb = int64_t(1) << (L - l);
+    int64_t tau = b / nb, nu = b % nb, p = tau >> 1;
+    return p * (nb << 1) + 2 * nu;
+  }
+  void validate() const;  // throws MHT_ERR_FORMAT on inconsistency
+};
+
+// --- Phi evaluators ------------------------------------------------------------------
+// Fill out (column-major nr x nc; complex: interleaved pairs) with Phi(rows, cols).
+struct Evaluator {
+  virtual ~Evaluator() = default;
+  virtual void eval(const int64_t* rows, int64_t nr, const int64_t* cols, int64_t nc,
+                    double* out) const = 0;
+};
+Evaluator* make_evaluator(const mht_problem& p);  // caller owns
+
+// --- trees -------------------------------------------------------------------------------
+void frequency_tree(const double* eigenvalues, int64_t m, int L, std::vector<int64_t>& perm,
+                    std::vector<int64_t>& off);
+void space_tree(const mht_problem& p, mht_tree_kind kind, int L, uint64_t seed,
+                std::vector<int64_t>& perm, std::vector<int64_t>& off);
+
+// --- interpolative decomposition ----------------------------------------------------------
+// Column ID of the column-major M x K matrix A (overwritten) by Householder QR with column
+// pivoting; rank = #{k : |R_kk| > eps |R_11|}.  Writes perm (skeleton first) and
+// T~ = R11^{-1} R12 (row-major r x (K-r)).  Returns r.
+int interpolative_decomposition_real(double* A, int64_t M, int64_t K, double eps,
+                                     std::vector<int32_t>& perm, std::vector<double>& T);
+int interpolative_decomposition_complex(std::complex<double>* A, int64_t M, int64_t K,
+                                        double eps, std::vector<int32_t>& perm,
+                                        std::vector<double>& T);
+
+// --- build ---------------------------------------------------------------------------------
+void build_factorization(const mht_problem& p, const mht_options& o, Factorization& F);
+void import_factors(const mht_factors& in, Factorization& F);
+
+// --- packing -------------------------------------------------------------------------------
+struct Stage {
+  int64_t nblocks = 0;
+  size_t desc_off = 0;          // byte offset of the MhtBlockDesc array
+  size_t items_syn_off = 0, items_adj_off = 0;
+  int64_t nitems_syn = 0, nitems_adj = 0;
+  int64_t out_entries = 0;      // entries of this stage's output vector (per RHS)
+  int64_t in_entries = 0;       // entries of its input vector (per RHS)
+  int64_t max_k = 0;            // largest K (ID) or |tau| (U)
+  int64_t max_rows = 0, max_cols = 0;
+  int64_t t_entries = 0;        // stored matrix entries
+  size_t data_bytes = 0;        // padded device bytes of the matrices
+  size_t alg_bytes = 0;         // algorithmic bytes of one single-RHS launch
+  int rows_per_item = 0, cols_per_item = 0;
+};
+
+struct Packed {
+  bool fp64 = false, cplx = false;
+  int elem_bytes = 4;           // bytes of one (possibly complex) element
+  std::vector<uint8_t> image;
+  size_t data_off = 0, index_off = 0, perm_off = 0, weights_off = 0;
+  std::vector<Stage> st;        // L+2 stages: ID levels 0..L, then U
+  int64_t vec_entries = 0;      // max butterfly-vector length (per RHS)
+  int64_t index_entries = 0;
+  size_t workspace_bytes(int64_t nrhs, int64_t n, int64_t m) const;
+};
+void pack(const Factorization& F, bool fp64, Packed& P);
+
+}  // namespace mht
+
+// Device binding and apply (implemented in the CUDA translation unit).
+namespace mht {
+struct Profiler;  // per-stage CUDA event records (apply.cu)
+struct DeviceView {
+  const uint8_t* base = nullptr;  // bound factor image
+  uint8_t* ws = nullptr;          // workspace
+  size_t ws_bytes = 0;
+  int64_t max_nrhs = 0;
+  Profiler* prof = nullptr;       // non-null while stage timing is enabled
+};
+Profiler* profiler_create();
+void profiler_destroy(Profiler* p);
+int profiler_read(Profiler* p, int direction, int nstages, double* ms, int64_t* launches, std::string& err);
+int apply_synthesize(const Factorization& F, const Packed& P, const DeviceView& d,
+                     const void* c, int64_t ldc, void* f, int64_t ldf, int64_t nrhs,
+                     bool weighted, mht_apply_mode mode, void* stream, std::string& err);
+int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, const void* f,
+                  int64_t ldf, void* c, int64_t ldc, int64_t nrhs, bool weighted,
+                  mht_apply_mode mode, void* stream, std::string& err);
+int64_t apply_launches(const Packed& P, int64_t nrhs, mht_apply_mode mode);
+int device_upload(void* dst, const void* src, size_t bytes, void* stream, std::string& err);
+int device_copy_async(void* dst, const void* src, size_t bytes, int kind, void* stream,
+                      std::string& err);
+int device_sync(void* stream, std::string& err);
+}  // namespace mht
+
+struct mht_plan {
+  mht::Factorization F;
+  mht::Packed P;
+  mht_apply_mode mode = MHT_APPLY_FP32;
+  double eps = 0;
+  double build_seconds = 0;
+  mht::DeviceView dev;
+  bool bound = false;
+  ~mht_plan() { mht::profiler_destroy(dev.prof); }
+};

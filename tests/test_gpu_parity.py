@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA apply (through the C ABI) against the FP64 oracle.
+
+The oracle builds its own factorization (scipy pivoted-QR IDs, its own trees); the same
+factors are imported into the library, and the GPU synthesis/adjoint are compared with the
+oracle's FP64 apply of those factors, element by element.  Tolerances (relative l2 per RHS,
+and max-abs relative to the largest output entry):
+  FP64 kernels:  1e-12      FP32 kernels: 1e-6
+The library's own host build plus the GPU apply is also checked against the dense transform
+(relative error within 10 eps + the kernel tolerance, the paper's "error about eps").
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import butterfly as B
+from oracle import dense as D
+from oracle import harmonics as H
+from tests._bridge import oracle_to_arrays
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-6, "3xtf32": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(mht_lib):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _rel(a, b):
+    a = np.asarray(a).reshape(len(a), -1)
+    b = np.asarray(b).reshape(len(b), -1)
+    per = np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+    elem = np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+    return float(per.max()), float(elem)
+
+
+def _to_dev(torch, x, plan):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(plan.dtype).cuda()
+
+
+def _check(got, ref, mode, factor=1.0):
+    rel, elem = _rel(got, ref)
+    tol = TOL[mode] * factor
+    assert rel <= tol, f"relative l2 error {rel:.3e} > {tol:.1e}"
+    assert elem <= 10 * tol, f"max element error {elem:.3e} > {10 * tol:.1e}"
+
+
+_CACHE = {}
+
+
+def _sphere_factors(n, lmax, leaf, eps):
+    key = ("s", n, lmax, leaf, eps)
+    if key not in _CACHE:
+        X = W.fibonacci_points(n)
+        Phi = H.sphere_phi(X, lmax)
+        m = Phi.shape[1]
+        _CACHE[key] = (B.build(B.dense_evaluator(Phi), n, m, W.sphere_eigenvalues(m), X, eps, leaf), Phi)
+    return _CACHE[key]
+
+
+def _torus_factors(n, m, leaf, eps):
+    key = ("t", n, m, leaf, eps)
+    if key not in _CACHE:
+        X = W.torus_points(n)
+        K = W.torus_modes(m)
+        Phi = H.torus_phi(X, K)
+        _CACHE[key] = (B.build(B.dense_evaluator(Phi), n, m, W.torus_eigenvalues(K), X, eps, leaf, "rect",
+                               complex_=True), Phi)
+    return _CACHE[key]
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 19])
+def test_sphere_synthesis_and_adjoint_match_oracle(torch_cuda, mode, nrhs):
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    n = 1000  # ragged: leaves of uneven size, L = 4
+    F, _ = _sphere_factors(n, 31, 64, 1e-6)
+    w = np.random.default_rng(0).uniform(0.5, 1.5, n)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode=mode, weights=w).bind(max_nrhs=nrhs)
+    C_ = W.gaussian_columns(F.m, nrhs, 11)
+    f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
+    _check(f, B.synthesize(F, C_), mode)
+    G = W.gaussian_columns(n, nrhs, 21)
+    a = plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy()
+    _check(a, B.analyze(F, G, w), mode)
+    a0 = plan.analyze_raw(_to_dev(torch, G, plan), weighted=False).cpu().numpy()
+    _check(a0, B.analyze(F, G), mode)
+    fw = plan.synthesize_raw(_to_dev(torch, C_, plan), weighted=True).cpu().numpy()
+    _check(fw, w[:, None] * B.synthesize(F, C_), mode)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+@pytest.mark.parametrize("nrhs", [1, 4, 9])
+def test_torus_complex_matches_oracle(torch_cuda, mode, nrhs):
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    F, _ = _torus_factors(1024, 1024, 64, 1e-10)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode=mode).bind(max_nrhs=nrhs)
+    C_ = W.gaussian_columns(F.m, nrhs, 3, complex_=True)
+    f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
+    _check(f, B.synthesize(F, C_), mode)
+    G = W.gaussian_columns(F.n, nrhs, 4, complex_=True)
+    a = plan.analyze_raw(_to_dev(torch, G, plan), weighted=False).cpu().numpy()
+    _check(a, B.analyze(F, G), mode)
+
+
+def test_larger_sphere_single_rhs(torch_cuda):
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    F, _ = _sphere_factors(4096, 63, 128, 1e-6)
+    for mode in ("fp32", "fp64"):
+        plan = Plan.from_factors(oracle_to_arrays(F), mode=mode).bind(max_nrhs=1)
+        c = W.sphere_coefficients(F.m)[:, 0]
+        _check(plan.synthesize_raw(_to_dev(torch, c, plan)).cpu().numpy(), B.synthesize(F, c), mode)
+        g = W.gaussian(F.n, 9)
+        _check(plan.analyze_raw(_to_dev(torch, g, plan)).cpu().numpy(), B.analyze(F, g), mode)
+
+
+def test_level_zero_and_empty_space_leaves(torch_cuda):
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    # L = 0: the whole transform is one ID plus one column basis
+    X = W.fibonacci_points(50)
+    Phi = H.sphere_phi(X, 6)
+    F0 = B.build(B.dense_evaluator(Phi), 50, 49, W.sphere_eigenvalues(49), X, 1e-7, 64)
+    assert F0.L == 0
+    # empty space leaves: all points in the first half of a given depth-3 tree
+    n = 96
+    X2 = W.fibonacci_points(n, seed=5)
+    Phi2 = H.sphere_phi(X2, 9)
+    perm = np.arange(n)
+    off = np.array([0, 30, 60, 60, 96, 96, 96, 96, 96])
+    F1 = B.build(B.dense_evaluator(Phi2), n, 100, W.sphere_eigenvalues(100), X2, 1e-7, 12,
+                 space=(perm, off))
+    assert F1.L == 3 and min(F1.ranks[3]) == 0
+    for F, nin in ((F0, 49), (F1, 100)):
+        for mode in ("fp32", "fp64"):
+            plan = Plan.from_factors(oracle_to_arrays(F), mode=mode).bind(max_nrhs=2)
+            C_ = W.gaussian_columns(nin, 2, 1)
+            _check(plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy(), B.synthesize(F, C_), mode)
+            G = W.gaussian_columns(F.n, 2, 2)
+            _check(plan.analyze_raw(_to_dev(torch, G, plan)).cpu().numpy(), B.analyze(F, G), mode)
+
+
+def test_zero_input_gives_zero_and_strided_leading_dimension(torch_cuda):
+    from paper_2605_21828_gb300 import Plan
+    import ctypes as C
+    from paper_2605_21828_gb300 import _lib
+    torch = torch_cuda
+    F, _ = _sphere_factors(1000, 31, 64, 1e-6)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode="fp32").bind(max_nrhs=3)
+    z = torch.zeros(F.m, dtype=torch.float32, device="cuda")
+    assert torch.count_nonzero(plan.synthesize_raw(z)).item() == 0
+    # ldc > m, ldf > n through the raw ABI
+    ldc, ldf, k = F.m + 7, F.n + 5, 3
+    C_ = W.gaussian_columns(F.m, k, 8)
+    cbuf = torch.zeros((k, ldc), dtype=torch.float32, device="cuda")
+    cbuf[:, :F.m] = torch.from_numpy(C_.T.copy()).float().cuda()
+    fbuf = torch.full((k, ldf), 7.0, dtype=torch.float32, device="cuda")
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _lib.check(_lib.load().mht_synthesize(plan._h, C.c_void_p(cbuf.data_ptr()), ldc, C.c_void_p(fbuf.data_ptr()),
+                                          ldf, k, s))
+    got = fbuf[:, :F.n].t().cpu().numpy()
+    _check(got, B.synthesize(F, C_), "fp32")
+    assert torch.all(fbuf[:, F.n:] == 7.0)  # padding untouched
+
+
+def test_host_transfer_entry_points(torch_cuda):
+    from paper_2605_21828_gb300 import Plan
+    F, _ = _torus_factors(1024, 1024, 64, 1e-10)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode="fp64").bind(max_nrhs=2)
+    C_ = W.gaussian_columns(F.m, 2, 5, complex_=True)
+    _check(plan.synthesize_host(C_), B.synthesize(F, C_), "fp64")
+    G = W.gaussian_columns(F.n, 2, 6, complex_=True)
+    _check(plan.analyze_host(G, weighted=False), B.analyze(F, G), "fp64")
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_library_build_plus_gpu_matches_dense_sphere(torch_cuda, mode):
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    n, eps = 4096, 1e-6
+    X = W.fibonacci_points(n)
+    Phi = H.sphere_phi(X, 63)
+    m = Phi.shape[1]
+    w = np.full(n, 4 * np.pi / n)
+    plan = Plan.build(n=n, m=m, eigenvalues=W.sphere_eigenvalues(m), evaluator="sphere", points=X, eps=eps,
+                      leaf_size=128, mode=mode, weights=w).bind(max_nrhs=4)
+    C_ = W.sphere_coefficients(m, 4)
+    f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
+    ref = D.synthesize(Phi, C_)
+    assert _rel(f, ref)[0] < 10 * eps + TOL[mode]
+    G = W.gaussian_columns(n, 4, 7)
+    a = plan.analyze_raw(_to_dev(torch, G, plan)).cpu().numpy()
+    assert _rel(a, D.analyze(Phi, G, w))[0] < 10 * eps + TOL[mode]
+
+
+def test_library_build_plus_gpu_torus_fp64_config(torch_cuda):
+    # flat periodic square, n = 4096 uniform random points, k in [-32, 31]^2, eps = 1e-10,
+    # leaf 64, complex128 coefficients, FP64 apply, checked against the dense NUDFT
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    n = m = 4096
+    eps = 1e-10
+    X = W.torus_points(n)
+    K = W.torus_modes(m)
+    plan = Plan.build(n=n, m=m, eigenvalues=W.torus_eigenvalues(K), evaluator="torus", points=X, torus_modes=K,
+                      eps=eps, leaf_size=64, mode="fp64").bind(max_nrhs=1)
+    c = W.gaussian(m, 1, True)
+    f = plan.synthesize_raw(_to_dev(torch, c, plan)).cpu().numpy()
+    Phi = H.torus_phi(X, K)
+    assert _rel(f, Phi @ c)[0] < 10 * eps
+    g = W.gaussian(n, 2, True)
+    a = plan.analyze_raw(_to_dev(torch, g, plan), weighted=False).cpu().numpy()
+    assert _rel(a, Phi.conj().T @ g)[0] < 10 * eps
+
+
+def test_autograd_matches_adjoint_and_finite_differences(torch_cuda):
+    from paper_2605_21828_gb300 import Plan, analyze, synthesize
+    torch = torch_cuda
+    F, Phi = _sphere_factors(1000, 31, 64, 1e-6)
+    w = np.random.default_rng(1).uniform(0.5, 1.5, F.n)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode="fp64", weights=w).bind(max_nrhs=1)
+    c = torch.from_numpy(W.gaussian(F.m, 3)).cuda().requires_grad_(True)
+    g = torch.from_numpy(W.gaussian(F.n, 4)).cuda()
+    loss = (synthesize(plan, c) * g).sum()
+    loss.backward()
+    # d/dc <Phi_eps c, g> = Phi_eps^T g (oracle adjoint); and the dense FP64 gradient Phi^T g
+    _check(c.grad.cpu().numpy(), B.analyze(F, W.gaussian(F.n, 4)), "fp64")
+    assert _rel(c.grad.cpu().numpy(), Phi.T @ W.gaussian(F.n, 4))[0] < 1e-5
+    # finite differences in FP64 along a random direction
+    d = torch.from_numpy(W.gaussian(F.m, 5)).cuda()
+    h = 1e-3
+    with torch.no_grad():
+        fd = ((synthesize(plan, c + h * d) * g).sum() - (synthesize(plan, c - h * d) * g).sum()) / (2 * h)
+    assert abs(fd.item() - (c.grad * d).sum().item()) < 1e-9 * abs(fd.item()) + 1e-9
+    # analysis: gradient of <Phi^H W f, h> w.r.t. f is W Phi h
+    f = torch.from_numpy(W.gaussian(F.n, 6)).cuda().requires_grad_(True)
+    hh = torch.from_numpy(W.gaussian(F.m, 7)).cuda()
+    (analyze(plan, f) * hh).sum().backward()
+    _check(f.grad.cpu().numpy(), w * B.synthesize(F, W.gaussian(F.m, 7)), "fp64")
+
+
+def test_launch_count_is_one_per_stage(torch_cuda):
+    from paper_2605_21828_gb300 import Plan
+    F, _ = _sphere_factors(1000, 31, 64, 1e-6)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode="fp32")
+    assert plan.launch_count(1) <= F.L + 2

@@ -1,0 +1,220 @@
+"""CPU tests of libmht: exported symbols, the FP64 host build, import/export, persistence
+and argument checking.  No compute call here touches a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import butterfly as B
+from oracle import dense as D
+from oracle import fem
+from oracle import harmonics as H
+from tests._bridge import arrays_to_oracle, oracle_to_arrays
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _plan_cls():
+    from paper_2605_21828_gb300 import Plan
+    return Plan
+
+
+def test_library_exports_every_declared_symbol(mht_lib):
+    hdr = open(os.path.join(ROOT, "include", "mht.h")).read()
+    declared = set(re.findall(r"^\s*(?:mht_status|const char\*)\s+(mht_[a-z0-9_]+)\s*\(", hdr, re.M))
+    assert len(declared) >= 18
+    for name in sorted(declared):
+        assert hasattr(mht_lib, name), name
+    from paper_2605_21828_gb300 import _lib
+    assert declared == set(_lib.SIGNATURES)
+
+
+def _sphere(n, lmax):
+    X = W.fibonacci_points(n)
+    Phi = H.sphere_phi(X, lmax)
+    return X, Phi, W.sphere_eigenvalues(Phi.shape[1])
+
+
+@pytest.mark.parametrize("tree", ["fiedler", "pca"])
+@pytest.mark.parametrize("oversample", [0.0, 2.0])
+def test_host_build_sphere_matches_dense(mht_lib, tree, oversample):
+    n, eps = 1024, 1e-6
+    X, Phi, lam = _sphere(n, 31)
+    w = np.full(n, 4 * np.pi / n)
+    p = _plan_cls().build(n=n, m=Phi.shape[1], eigenvalues=lam, evaluator="sphere", points=X,
+                          eps=eps, leaf_size=64, tree=tree, oversample=oversample, weights=w)
+    F = arrays_to_oracle(p.export())
+    assert F.L == 4
+    c = W.sphere_coefficients(Phi.shape[1])[:, 0]
+    ref = Phi @ c
+    assert np.linalg.norm(B.synthesize(F, c) - ref) / np.linalg.norm(ref) < 10 * eps
+    g = W.gaussian(n, 3)
+    refa = D.analyze(Phi, g, w)
+    assert np.linalg.norm(B.analyze(F, g, w) - refa) / np.linalg.norm(refa) < 10 * eps
+
+
+def test_host_build_torus_matches_nudft(mht_lib):
+    n = m = 1024
+    eps = 1e-10
+    X = W.torus_points(n)
+    K = W.torus_modes(m)
+    Phi = H.torus_phi(X, K)
+    p = _plan_cls().build(n=n, m=m, eigenvalues=W.torus_eigenvalues(K), evaluator="torus",
+                          points=X, torus_modes=K, eps=eps, leaf_size=64, mode="fp64")
+    d = p.export()
+    assert d["complex"]
+    F = arrays_to_oracle(d)
+    c = W.gaussian(m, 1, True)
+    ref = Phi @ c
+    assert np.linalg.norm(B.synthesize(F, c) - ref) / np.linalg.norm(ref) < 10 * eps
+    g = W.gaussian(n, 2, True)
+    refa = Phi.conj().T @ g
+    assert np.linalg.norm(B.analyze(F, g) - refa) / np.linalg.norm(refa) < 10 * eps
+
+
+def test_rect_tree_and_frequency_tree_match_oracle(mht_lib):
+    n = m = 1024
+    X = W.torus_points(n, seed=4)
+    K = W.torus_modes(m)
+    lam = W.torus_eigenvalues(K)
+    p = _plan_cls().build(n=n, m=m, eigenvalues=lam, evaluator="torus", points=X, torus_modes=K,
+                          eps=1e-4, leaf_size=64, tree="rect")
+    d = p.export()
+    sp, so = B.space_tree(X, p.levels, "rect")
+    mp, mo = B.frequency_tree(lam, p.levels)
+    assert np.array_equal(d["mode_perm"], mp) and np.array_equal(d["mode_offsets"], mo)
+    assert np.array_equal(d["space_offsets"], so)
+    for t in range(len(so) - 1):
+        assert set(d["space_perm"][so[t]:so[t + 1]]) == set(sp[so[t]:so[t + 1]])
+
+
+def test_fiedler_tree_separates_clusters(mht_lib):
+    rng = np.random.default_rng(3)
+    X = np.vstack([rng.standard_normal((40, 3)) * 0.1, rng.standard_normal((40, 3)) * 0.1 + [5, 0, 0]])
+    lam = np.arange(80.0)
+    Phi = rng.standard_normal((80, 80))
+    p = _plan_cls().build(n=80, m=80, eigenvalues=lam, evaluator="dense", dense=Phi, points=X,
+                          eps=1e-8, levels=1, tree="fiedler")
+    d = p.export()
+    left = set(d["space_perm"][:d["space_offsets"][1]].tolist())
+    assert left in (set(range(40)), set(range(40, 80)))
+
+
+def test_import_export_roundtrip(mht_lib):
+    n = 256
+    X, Phi, lam = _sphere(n, 15)
+    F = B.build(B.dense_evaluator(Phi), n, 256, lam, X, 1e-6, 32)
+    arr = oracle_to_arrays(F)
+    p = _plan_cls().from_factors(arr, mode="fp64")
+    back = p.export()
+    for key in ("space_perm", "space_offsets", "mode_perm", "mode_offsets", "ranks", "local_perm"):
+        assert np.array_equal(np.asarray(back[key]), np.asarray(arr[key])), key
+    assert np.array_equal(back["transfer"], arr["transfer"])
+    assert np.array_equal(back["column_bases"], arr["column_bases"])
+    info = p.info()
+    assert info["stored_entries"] == F.stored_entries()
+    assert sum(p.level_info(l)["transfer_entries"] for l in range(p.levels + 2)) == F.stored_entries()
+
+
+def test_import_rejects_inconsistent_factors(mht_lib):
+    from paper_2605_21828_gb300 import MhtError
+    n = 128
+    X, Phi, lam = _sphere(n, 11)
+    F = B.build(B.dense_evaluator(Phi), n, 144, lam, X, 1e-6, 32)
+    arr = oracle_to_arrays(F)
+    bad = dict(arr)
+    bad["local_perm"] = arr["local_perm"].copy()
+    bad["local_perm"][0] = bad["local_perm"][1]  # not a permutation
+    with pytest.raises(MhtError, match="FORMAT"):
+        _plan_cls().from_factors(bad)
+    bad = dict(arr)
+    bad["space_perm"] = arr["space_perm"].copy()
+    bad["space_perm"][0] = bad["space_perm"][1]
+    with pytest.raises(MhtError, match="FORMAT"):
+        _plan_cls().from_factors(bad)
+
+
+def test_save_load_roundtrip_and_corruption(mht_lib, tmp_path):
+    from paper_2605_21828_gb300 import MhtError
+    n = 512
+    X, Phi, lam = _sphere(n, 21)
+    m = 484
+    p = _plan_cls().build(n=n, m=m, eigenvalues=lam[:m], evaluator="dense", dense=Phi[:, :m],
+                          points=X, eps=1e-7, leaf_size=64, weights=np.full(n, 2.0))
+    path = str(tmp_path / "plan.bin")
+    p.save(path)
+    q = _plan_cls().load(path, mode="fp64")
+    a, b = p.export(), q.export()
+    for k in a:
+        if isinstance(a[k], np.ndarray):
+            assert np.array_equal(a[k], b[k]), k
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 0xFF
+    bad = str(tmp_path / "bad.bin")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(MhtError, match="FORMAT"):
+        _plan_cls().load(bad)
+    open(bad, "wb").write(bytes(raw[:50]))
+    with pytest.raises(MhtError, match="FORMAT"):
+        _plan_cls().load(bad)
+    open(bad, "wb").write(b"not a plan file at all........")
+    with pytest.raises(MhtError, match="FORMAT"):
+        _plan_cls().load(bad)
+
+
+def test_callback_evaluator_equals_dense_and_propagates_errors(mht_lib):
+    from paper_2605_21828_gb300 import MhtError
+    n = 256
+    X, Phi, lam = _sphere(n, 15)
+    kw = dict(n=n, m=256, eigenvalues=lam, points=X, eps=1e-6, leaf_size=32, oversample=0)
+    a = _plan_cls().build(evaluator="dense", dense=Phi, **kw).export()
+    b = _plan_cls().build(evaluator="callback", callback=lambda r, c: Phi[np.ix_(r, c)], **kw).export()
+    assert np.array_equal(a["ranks"], b["ranks"]) and np.array_equal(a["transfer"], b["transfer"])
+
+    def broken(r, c):
+        raise RuntimeError("evaluator failure")
+
+    with pytest.raises(MhtError, match="CALLBACK"):
+        _plan_cls().build(evaluator="callback", callback=broken, **kw)
+
+
+def test_invalid_arguments_and_unbound_apply(mht_lib):
+    from paper_2605_21828_gb300 import MhtError, _lib
+    n = 64
+    X, Phi, lam = _sphere(n, 7)
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        _plan_cls().build(n=n, m=64, eigenvalues=lam, evaluator="sphere", points=X, eps=2.0)
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        _plan_cls().build(n=n, m=64, eigenvalues=lam, evaluator="torus", points=X, eps=1e-6)
+    bad = lam.copy()
+    bad[3] = np.nan
+    with pytest.raises(MhtError, match="NUMERIC"):
+        _plan_cls().build(n=n, m=64, eigenvalues=bad, evaluator="sphere", points=X, eps=1e-6)
+    p = _plan_cls().build(n=n, m=64, eigenvalues=lam, evaluator="sphere", points=X, eps=1e-6, leaf_size=16)
+    lib = _lib.load()
+    dummy = C.c_void_p(256)
+    st = lib.mht_synthesize(p._h, dummy, 64, dummy, 64, 1, None)
+    assert st == 9 and b"bound" in lib.mht_last_error()
+    st = lib.mht_plan_bind_device(p._h, C.c_void_p(0), 0, C.c_void_p(0), 0, 1, None)
+    assert st == 1
+    st = lib.mht_plan_bind_device(p._h, C.c_void_p(256), 16, C.c_void_p(512), 16, 1, None)
+    assert st == 2  # buffers too small: rejected before any device call
+
+
+def test_fem_dense_build_and_analysis_inverts_synthesis(mht_lib):
+    V, F_ = W.deformed_icosphere(3)
+    lam, Phi, Md, K = fem.laplace_beltrami_basis(V, F_, 160)
+    n = len(V)
+    eps = 1e-8
+    p = _plan_cls().build(n=n, m=160, eigenvalues=lam, evaluator="dense", dense=Phi, points=V,
+                          eps=eps, leaf_size=64, weights=Md)
+    F = arrays_to_oracle(p.export())
+    c = W.gaussian(160, 5)
+    f = B.synthesize(F, c)
+    assert np.linalg.norm(f - Phi @ c) / np.linalg.norm(Phi @ c) < 10 * eps
+    # Phi^T M Phi = I, so analysis (weights = lumped mass) undoes synthesis
+    c2 = B.analyze(F, f, Md)
+    assert np.linalg.norm(c2 - c) / np.linalg.norm(c) < 1e-6
