@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the BF-MHT apply on GB300: transforms/s (synthesis + adjoint) and roofline.
+
+Workload (default): the unit sphere, n = 65536 jittered-Fibonacci points, m = 65536 real
+spherical harmonics up to degree 255, eps = 1e-6, leaf size 128, FP32 apply, analysis
+weights 4 pi / n.  One step = one synthesis f = Phi c plus one weighted analysis
+c = Phi^T W f of `--nrhs` vectors; value = vectors transformed (both directions) per second
+over all ranks.  Inputs are resident in HBM; the packed factors (GBs) are far larger than
+L2, so every step streams them from HBM (no flush needed).
+
+`--impl reference` times the FP64 CPU oracle (direct summation with matrix-free rows of
+Phi) on a bounded sample of rows per step, scaled to whole transforms.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transforms/s (synthesis + weighted adjoint)"
+WORKLOADS = {
+    # name: (n, lmax, leaf, eps)
+    "sphere65536": (65536, 255, 128, 1e-6),
+    "sphere16384": (16384, 127, 128, 1e-6),   # small case for profiler captures
+    "sphere4096": (4096, 63, 128, 1e-6),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--multi-rhs", type=int, default=64, help="extra measurement at this many RHS (0: off)")
+    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS))
+    ap.add_argument("--plan-cache", default=os.environ.get("MHT_PLAN_CACHE", ""))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(name):
+    n, lmax, leaf, eps = WORKLOADS[name]
+    return {"workload": f"unit sphere: n={n} jittered-Fibonacci points, m={(lmax + 1) ** 2} real spherical "
+                        f"harmonics (degree <= {lmax}), eps={eps:g}, leaf {leaf}, FP32 factors, weights 4pi/n",
+            "n": n, "m": (lmax + 1) ** 2, "eps": eps, "leaf_size": leaf,
+            "l2": "packed factors >> 129 MB L2 (streamed from HBM every step; no flush needed)"}
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+def oracle_sample_step(X, c, w, rows, lmax):
+    """Oracle direct summation restricted to `rows`: f(rows) = Phi(rows,:) c and the
+    contribution Phi(rows,:)^T (w f)(rows) to the adjoint.  Returns seconds."""
+    import numpy as np
+
+    from oracle import harmonics as H
+    t0 = time.perf_counter()
+    Phi = H.sphere_phi(X[rows], lmax)
+    f = Phi @ c
+    _ = Phi.T @ (w[rows] * f)
+    dt = time.perf_counter() - t0
+    del Phi
+    np.asarray(f)
+    return dt
+
+
+def cpu_baseline(name, budget_s=15.0, steps=None):
+    import numpy as np
+
+    import workloads as W
+    n, lmax, leaf, eps = WORKLOADS[name]
+    X = W.fibonacci_points(n)
+    m = (lmax + 1) ** 2
+    c = W.sphere_coefficients(m)[:, 0]
+    w = np.full(n, 4 * np.pi / n)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(n, 256, replace=False))
+    t = oracle_sample_step(X, c, w, rows, lmax)
+    per_row = t / len(rows)
+    s = int(min(n, max(256, budget_s / max(per_row, 1e-9) / (steps or 1))))
+    rows = np.sort(rng.choice(n, s, replace=False))
+    times = [oracle_sample_step(X, c, w, rows, lmax) for _ in range(steps or 1)]
+    t_full = statistics.median(times) * n / s
+    cores = len(os.sched_getaffinity(0))
+    return 1.0 / t_full, {"kind": "oracle", "cores": cores,
+                          "sample": f"{s} of {n} rows per step (Phi rows by the normalized Legendre recurrence, "
+                                    f"f = Phi c and Phi^T W f restricted to them), scaled by n/{s}; numpy/BLAS "
+                                    f"threads on {cores} cores"}, times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    desc = workload_desc(args.workload)
+    steps = max(1, args.steps)
+    for _ in range(max(0, args.warmup)):
+        pass  # the oracle has no warm state; warm-up steps are not needed
+    value, cb, times = cpu_baseline(args.workload, budget_s=min(120.0, 4.0 * steps), steps=steps)
+    ms = 1000.0 / value
+    cb["value"] = value
+    cb["unit"] = "transforms/s"
+    line = {"impl": "reference", "metric": METRIC,
+            "value": value, "unit": "transforms/s", "n_gpus": args.gpus, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = [[x.strip() for x in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
+        if len({r[0] for r in rows}) > 1:  # several GPUs visible: keep this rank's
+            rows = [r for r in rows if r[0] == str(gpu_index)]
+        for p in rows:
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def get_plan(args, dist, rank):
+    import numpy as np
+
+    import workloads as W
+    from paper_2605_21828_gb300 import Plan
+    n, lmax, leaf, eps = WORKLOADS[args.workload]
+    m = (lmax + 1) ** 2
+    cache = args.plan_cache or os.path.join(tempfile.gettempdir(), f"mht_{args.workload}.plan")
+    t0 = time.time()
+    built = False
+    if rank == 0 and not os.path.exists(cache):
+        X = W.fibonacci_points(n)
+        plan = Plan.build(n=n, m=m, eigenvalues=W.sphere_eigenvalues(m), evaluator="sphere", points=X, eps=eps,
+                          leaf_size=leaf, mode="fp32", weights=np.full(n, 4 * np.pi / n))
+        built = True
+        if dist is not None or args.plan_cache:
+            plan.save(cache)
+    if dist is not None:
+        dist.barrier()
+    if not built:
+        plan = Plan.load(cache, mode="fp32")
+    return plan, time.time() - t0, built
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2605_21828_gb300.build import build_library
+    build_library()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    plan, setup_s, built = get_plan(args, dist, rank)
+    info = plan.info()
+    K, Wm = args.steps, args.warmup
+    nrhs = args.nrhs
+    max_nrhs = max(nrhs, args.multi_rhs or 1)
+    plan.bind(device=dev, max_nrhs=max_nrhs)
+    n, m = plan.n, plan.m
+    c = torch.from_numpy(W.sphere_coefficients(m, nrhs)).float().to(dev)
+    c = c[:, 0].contiguous() if nrhs == 1 else c
+    stream = torch.cuda.current_stream(dev)
+
+    def step(x):
+        f = plan.synthesize_raw(x)
+        return plan.analyze_raw(f, weighted=True)
+
+    clocks = ClockSampler()
+    clocks.start()
+    for _ in range(max(Wm, 3)):
+        step(c)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(K):
+        step(c)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    # the same K steps again with CUDA events around every kernel launch (per-stage times)
+    plan.profile(True)
+    for _ in range(K):
+        step(c)
+    torch.cuda.synchronize()
+    syn_ms, syn_n = plan.stage_times(0)
+    adj_ms, adj_n = plan.stage_times(1)
+    plan.profile(False)
+    clk = clocks.stop(local)
+    status = plan.check()
+    if dist is not None:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / K
+    value = world * K * nrhs / (ms_total / 1000.0)
+
+    # per-stage roofline: the dominant kernel is the one with the most device time
+    L = plan.levels
+    stages = [plan.level_info(s) for s in range(L + 2)]
+    kern = {
+        "k_synth (transfer levels 0..L)": (syn_ms[:L + 1].sum(), syn_n[:L + 1].sum(),
+                                           sum(stages[s]["algorithmic_bytes"] * syn_n[s] for s in range(L + 1))),
+        "k_adjoint (transfer levels L..0)": (adj_ms[:L + 1].sum(), adj_n[:L + 1].sum(),
+                                             sum(stages[s]["algorithmic_bytes"] * adj_n[s] for s in range(L + 1))),
+        "k_synth (column bases U)": (syn_ms[L + 1], syn_n[L + 1], stages[L + 1]["algorithmic_bytes"] * syn_n[L + 1]),
+        "k_adjoint (column bases U)": (adj_ms[L + 1], adj_n[L + 1], stages[L + 1]["algorithmic_bytes"] * adj_n[L + 1]),
+    }
+    name, (kms, kl, kbytes) = max(kern.items(), key=lambda kv: kv[1][0])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = (kbytes / 1e9) / (kms / 1e3) if kms > 0 else 0.0
+    step_bytes = sum(stages[s]["algorithmic_bytes"] * (syn_n[s] + adj_n[s]) for s in range(L + 2)) / K
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else
+                "fallback 6800 GB/s", "traffic": None, "launches": int(kl), "avg_launch_ms": kms / max(kl, 1),
+                "step_algorithmic_GB": step_bytes / 1e9,
+                "step_frac": (step_bytes / 1e9) / (ms_step / 1e3) / peak}
+    per_stage = {"synth_ms": [round(x / K, 5) for x in syn_ms], "adjoint_ms": [round(x / K, 5) for x in adj_ms],
+                 "algorithmic_MB": [round(s["algorithmic_bytes"] / 1e6, 3) for s in stages]}
+
+    # multi-RHS measurement (same step, more vectors per launch)
+    multi = None
+    if args.multi_rhs and args.multi_rhs > 1:
+        km = args.multi_rhs
+        C = torch.from_numpy(W.sphere_coefficients(m, km)).float().to(dev)
+        for _ in range(3):
+            step(C)
+        torch.cuda.synchronize()
+        reps = max(3, K // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            step(C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mms = e0.elapsed_time(e1) / reps
+        multi = {"nrhs": km, "ms_per_step": mms, "transforms_per_s": world * km / (mms / 1e3),
+                 "mode": "fp32 SIMT"}
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        import ctypes as Cc
+
+        from paper_2605_21828_gb300 import _lib
+        lib = _lib.load()
+        ch = torch.from_numpy(W.sphere_coefficients(m, nrhs)).float().pin_memory()
+        fh = torch.empty((nrhs, n), dtype=torch.float32).pin_memory()
+        ch2 = torch.empty((nrhs, m), dtype=torch.float32).pin_memory()
+        chc = ch.t().contiguous().pin_memory()  # column-major m x nrhs
+        s = Cc.c_void_p(stream.cuda_stream)
+
+        def host_step():
+            _lib.check(lib.mht_synthesize_host(plan._h, Cc.c_void_p(chc.data_ptr()), m, Cc.c_void_p(fh.data_ptr()),
+                                               n, nrhs, s))
+            _lib.check(lib.mht_analyze_host(plan._h, Cc.c_void_p(fh.data_ptr()), n, Cc.c_void_p(ch2.data_ptr()),
+                                            m, nrhs, 1, s))
+        for _ in range(3):
+            host_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            host_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * K * nrhs / dt, "unit": "transforms/s",
+               "h2d_bytes_per_step": (m + n) * 4 * nrhs, "d2h_bytes_per_step": (n + m) * 4 * nrhs,
+               "api": "mht_synthesize_host + mht_analyze_host (pinned host buffers)"}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, meta, _ = cpu_baseline(args.workload, budget_s=15.0)
+        cb = dict(meta, value=v, unit="transforms/s")
+
+    launches = int(syn_n.sum() + adj_n.sum())  # launches of the K profiled steps = K steps' launches
+    desc = workload_desc(args.workload)
+    desc.update({"nrhs": nrhs, "levels": L, "stored_entries": info["stored_entries"],
+                 "factor_GB": info["factor_bytes"] / 1e9, "compression_vs_dense": n * m / info["stored_entries"],
+                 "plan_setup_s": round(setup_s, 1), "plan_built_here": built, "parallelism": f"replicas x{world}"})
+    line = {"metric": METRIC, "value": value,
+            "unit": "transforms/s", "n_gpus": world, "steps": K, "warmup": max(Wm, 3), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": desc, "roofline": roofline, "per_stage": per_stage,
+            "multi_rhs": multi, "e2e": e2e, "cpu_baseline": cb, "clocks": clk, "gpu_launches": launches,
+            "device_status": status}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -76,6 +76,13 @@ typedef enum {
 } mht_tree_kind;
 
 typedef enum {
+  MHT_ID_AUTO = 0,      /* BLOCKED for large problems (n m >= 2^28), else CLASSICAL          */
+  MHT_ID_CLASSICAL = 1, /* Householder QR with column pivoting, one column at a time        */
+  MHT_ID_BLOCKED = 2    /* QR with randomized block pivoting (Gaussian sketch of b + 8 rows
+                           picks 64 pivots at a time; compact-WY panel updates); large blocks */
+} mht_id_method;
+
+typedef enum {
   MHT_EVAL_CALLBACK = 0, /* problem->eval(ctx, rows, nrows, cols, ncols, out)           */
   MHT_EVAL_TORUS = 1,    /* Phi_jk = exp(i k_k . x_j), Eq. 2D-DFT; points (n x 2),
                             problem->torus_modes (m x 2 int64); field must be COMPLEX   */
@@ -118,8 +125,10 @@ typedef struct {
   mht_tree_kind tree;
   uint64_t seed;       /* row sampling and Lanczos start vectors                       */
   int32_t num_threads; /* host threads for the build; 0 = OpenMP default               */
-  double oversample;   /* row-sampled IDs use min(|tau|, ceil(oversample * K) + 16) rows;
-                          <= 0 disables sampling (exact IDs on all rows)                */
+  double oversample;   /* row-sampled IDs use min(|tau|, ceil(oversample * K) + 16) rows, a
+                          heuristic that costs accuracy at tight eps; <= 0 disables
+                          sampling (exact IDs on all rows, the recommended setting)     */
+  mht_id_method id_method; /* pivoting strategy of the real IDs (complex IDs: classical) */
 } mht_options;
 
 /* Factors as plain arrays: the content of a factorization, in the notation of Sec. 2.
@@ -244,12 +253,25 @@ mht_status mht_analyze_host(mht_plan* plan, const void* f_host, int64_t ldf, voi
 /* Number of kernel launches one mht_synthesize / mht_analyze call makes for nrhs. */
 mht_status mht_apply_launch_count(const mht_plan* plan, int64_t nrhs, int64_t* launches);
 
+/* Reads and clears the device status word of the bound workspace (synchronizes `stream`).
+ * Kernels set bit 0 when a bounded wait for a bulk copy gives up instead of spinning
+ * forever; the affected outputs are then unspecified.  Returns MHT_OK with *flags = 0 when
+ * every wait since the last check completed, MHT_ERR_TIMEOUT (and the flags) otherwise. */
+mht_status mht_plan_check(mht_plan* plan, void* stream, int32_t* flags);
+
+/* Apply path: 0 = automatic (one persistent launch per direction that runs every stage
+ * when up to 8 RHS fit its shared memory, otherwise one launch per stage), 1 = always one
+ * launch per stage, 2 = always the persistent launch (MHT_ERR_UNSUPPORTED if it does not
+ * fit).  Both paths compute the same result. */
+mht_status mht_plan_set_path(mht_plan* plan, int32_t path);
+
 /* Stage timing for benchmarks.  While enabled, every apply on the plan records a CUDA
- * event before and after each stage's kernel launch (on the apply's stream).
+ * event before and after each kernel launch (on the apply's stream).
  * mht_plan_stage_times waits for the recorded events, returns the summed milliseconds and
- * launch counts per stage (arrays of L+2 entries: ID levels 0..L, then the column bases)
- * for direction 0 (synthesis) or 1 (analysis), and clears the record.  Enabling costs one
- * event record per launch; disabled (the default) it costs nothing. */
+ * launch counts (arrays of L+3 entries: ID levels 0..L and the column bases for per-stage
+ * launches, then entry L+2 for persistent launches that run all stages) for direction 0
+ * (synthesis) or 1 (analysis), and clears the record.  Enabling costs one event record per
+ * launch; disabled (the default) it costs nothing. */
 mht_status mht_plan_profile(mht_plan* plan, int32_t enable);
 mht_status mht_plan_stage_times(mht_plan* plan, int32_t direction, double* ms, int64_t* launches);
 

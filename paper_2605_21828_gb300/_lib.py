@@ -33,7 +33,7 @@ class Problem(C.Structure):
 class Options(C.Structure):
     _fields_ = [("eps", C.c_double), ("leaf_size", C.c_int64), ("levels", C.c_int32),
                 ("mode", C.c_int), ("tree", C.c_int), ("seed", C.c_uint64),
-                ("num_threads", C.c_int32), ("oversample", C.c_double)]
+                ("num_threads", C.c_int32), ("oversample", C.c_double), ("id_method", C.c_int)]
 
 
 class Factors(C.Structure):
@@ -81,6 +81,8 @@ SIGNATURES = {
     "mht_analyze_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
                                    C.c_void_p]),
     "mht_apply_launch_count": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "mht_plan_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "mht_plan_set_path": (C.c_int, [C.c_void_p, C.c_int32]),
     "mht_plan_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "mht_plan_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mht_plan_save": (C.c_int, [C.c_void_p, C.c_char_p]),

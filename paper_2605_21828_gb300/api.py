@@ -28,10 +28,13 @@ def _dptr(a: np.ndarray, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
 
 
+_IDS = {"auto": 0, "classical": 1, "blocked": 2}
+
+
 def _options(eps=1e-6, leaf_size=128, levels=-1, mode="fp32", tree="auto", seed=0,
-             num_threads=0, oversample=2.0):
+             num_threads=0, oversample=0.0, id_method="auto"):
     return L.Options(eps, leaf_size, levels, _MODES[mode], _TREES[tree], seed, num_threads,
-                     oversample)
+                     oversample, _IDS[id_method])
 
 
 class Plan:
@@ -211,12 +214,25 @@ class Plan:
         L.check(L.load().mht_apply_launch_count(self._h, nrhs, C.byref(v)))
         return int(v.value)
 
+    def check(self):
+        """Raises MhtError(TIMEOUT) if a kernel gave up a bounded wait since the last check."""
+        import torch
+        f = C.c_int32()
+        s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        L.check(L.load().mht_plan_check(self._h, s, C.byref(f)))
+        return int(f.value)
+
+    def set_path(self, path: str = "auto"):
+        """'auto', 'staged' (one launch per stage) or 'fused' (one persistent launch)."""
+        L.check(L.load().mht_plan_set_path(self._h, {"auto": 0, "staged": 1, "fused": 2}[path]))
+        return self
+
     def profile(self, enable: bool = True):
         L.check(L.load().mht_plan_profile(self._h, 1 if enable else 0))
 
     def stage_times(self, direction: int):
-        """(ms[L+2], launches[L+2]) summed since the last read (direction 0 synth, 1 analyze)."""
-        ns = self.levels + 2
+        """(ms[L+3], launches[L+3]) summed since the last read (direction 0 synth, 1 analyze)."""
+        ns = self.levels + 3
         ms = (C.c_double * ns)()
         ln = (C.c_int64 * ns)()
         L.check(L.load().mht_plan_stage_times(self._h, direction, ms, ln))

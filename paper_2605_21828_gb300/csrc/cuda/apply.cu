@@ -7,12 +7,19 @@
 //     synthesis  y_i = x[skel_i] + sum_j T~_ij x[rest_j]
 //     adjoint    u[skel_i] = z_i,   u[rest_j] = sum_i conj(T~_ij) z_i
 // and the column-basis stage is a dense block product.  Each stored matrix is read exactly
-// once per apply (the paper's observation that apply cost equals storage, Sec. 6.2), so
-// the single-RHS apply is bound by HBM bandwidth: the kernels stream each matrix with
-// 128-bit non-allocating loads, gather the short input vector into shared memory, and
-// reduce with warp shuffles.  The adjoint is a gather: the two sibling blocks (2p, nu),
-// (2p+1, nu) that share an input pair write two separate buffers, and the next stage sums
-// them while loading -- no atomics, deterministic results.
+// once per apply (apply cost equals storage, Sec. 6.2), so the single-RHS apply is bound by
+// HBM bandwidth.  The packed plan holds every matrix in both orientations, so both
+// directions are "rows times a gathered vector":
+//   * one CTA per work item (block, row range of ~32 KB);
+//   * thread 0 stages the item's rows into shared memory with one 1-D TMA bulk copy
+//     (cp.async.bulk, completion on an mbarrier) while all threads gather the block's
+//     input vector from L2 into shared memory;
+//   * each warp then reduces whole rows from shared memory with 128-bit loads and warp
+//     shuffles.
+// The adjoint is a gather: the sibling blocks (2p, nu), (2p+1, nu) that share an input pair
+// write separate buffers and the next stage sums them while loading -- no atomics, so the
+// result is deterministic.  Every mbarrier wait is bounded; on timeout the kernel sets a bit
+// in the workspace status word (read by mht_plan_check) instead of hanging.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,28 +34,62 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits give up after 2 s
 
-__device__ __forceinline__ uint4 ldg_stream(const void* p) {
-  uint4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
+enum Mode { SYN_ID = 0, ADJ_ID = 1, SYN_U = 2, ADJ_U = 3 };
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity; gives up after kWaitNs of wall time, or as soon
+// as *abort_flag is non-zero (when given).  Returns false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase,
+                                                  const unsigned* abort_flag = nullptr) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if ((it & 255) == 0) {
+      if (globaltimer_ns() - t0 > kWaitNs) return false;
+      if (abort_flag && *reinterpret_cast<const volatile unsigned*>(abort_flag) != 0u) return false;
+    }
+  }
 }
 
 template <class R>
-struct Vec16 {
+struct alignas(16) Vec16 {  // one 128-bit load / store
   static constexpr int NS = 16 / sizeof(R);
   R s[NS];
 };
-
-template <class R>
-__device__ __forceinline__ Vec16<R> load16(const R* p) {
-  uint4 u = ldg_stream(p);
-  Vec16<R> v;
-  memcpy(&v, &u, 16);
-  return v;
-}
 
 template <class R>
 __device__ __forceinline__ R warp_sum(R v) {
@@ -58,59 +99,108 @@ __device__ __forceinline__ R warp_sum(R v) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Synthesis, one work item = (block, rows [start, start+count)), RT right-hand sides.
-//   ID stage (U_STAGE = false):  y[out_off + i] = x[idx[i]] + T~[i,:] . x[idx[r + :]]
-//   U stage  (U_STAGE = true):   f[perm[out_off + i]] = U[i,:] . y_L[in_off + :]
-// Element strides: input x[e * xs_e + k * xs_k], output y[e * ys_e + k * ys_k] (in elements;
-// one complex value is one element).
-template <class R, bool C, int RT, bool U_STAGE>
+// out[o(i)] = ident(i) + sum_j M[i, j] x[j] for the rows i of one work item.
+//   SYN_ID: M = T~ (r x K'),           x[j] = in[idx[r + j]],   o(i) = out_off + i,
+//           ident(i) = in[idx[i]]
+//   ADJ_ID: M = conj(T~)^T (K' x r),   x[j] = z0[out_off + j] (+ z1[...]),
+//           o(i) = idx[r + i] in the sibling buffer; skeleton out[idx[j]] = x[j]
+//   SYN_U:  M = U (|tau| x r_L),       x[j] = yL[in_off + j],   o(i) = perm[out_off + i]
+//           (times w[o(i)] when weights are given)
+//   ADJ_U:  M = conj(U)^T (r_L x |tau|), x[j] = w[p] f[p] with p = perm[out_off + j],
+//           o(i) = in_off + i
+// Element strides: in[e * is_e + k * is_k], out[e * os_e + k * os_k]; one complex value is
+// one element.  RT right-hand sides per CTA (blockIdx.y selects the RHS tile).
+template <class R, bool C, int RT, int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_synth(const R* __restrict__ data, const int* __restrict__ idx, const MhtBlockDesc* __restrict__ desc,
-        const MhtItem* __restrict__ items, const int* __restrict__ perm, const R* __restrict__ wts,
-        const R* __restrict__ x, long long xs_e, long long xs_k,
-        R* __restrict__ y, long long ys_e, long long ys_k, int nrhs) {
+k_rowdot(const R* __restrict__ data, const int* __restrict__ idx, const MhtBlockDesc* __restrict__ desc,
+         const MhtItem* __restrict__ items, const int* __restrict__ perm, const R* __restrict__ wts,
+         const R* __restrict__ in0, const R* __restrict__ in1, long long is_e, long long is_k,
+         R* __restrict__ out0, R* __restrict__ out1, long long os_e, long long os_k, int nrhs,
+         int tile_bytes_max, int ldx_max, unsigned* __restrict__ status) {
   constexpr int W = C ? 2 : 1;
   constexpr int NS = 16 / sizeof(R);
   constexpr int E = NS / W;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* xs = reinterpret_cast<R*>(smem_raw);  // [RT][ldt][W], each RHS row 16-byte aligned
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  R* tile = reinterpret_cast<R*>(smem_raw + 128);
+  R* xs = reinterpret_cast<R*>(smem_raw + 128 + ((tile_bytes_max + 127) / 128) * 128);  // [RT][ldx][W]
 
   const MhtItem it = items[blockIdx.x];
   const MhtBlockDesc d = desc[it.blk];
   const int k0 = blockIdx.y * RT;
   const int nk = min(RT, nrhs - k0);
   const int ldt = d.ldt;
+  const unsigned bytes = unsigned(it.count) * unsigned(ldt) * unsigned(W * sizeof(R));
+  R* out = (MODE == ADJ_ID && it.sib) ? out1 : out0;
 
-  // gather the input columns of the matrix (zero padding up to ldt, and beyond nk)
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && bytes > 0) {
+    mbar_expect_tx(bar, bytes);
+    bulk_copy_g2s(tile, data + (d.t_off + (long long)it.start * ldt) * W, bytes, bar);
+  }
+
+  // gather the input vector while the tile is in flight (zero padding to ldt and beyond nk)
   for (int j = threadIdx.x; j < ldt; j += kThreads) {
     long long src = -1;
-    if (j < d.cols) src = U_STAGE ? (long long)(d.in_off + j) : (long long)idx[d.idx_off + d.rows + j];
+    R w = R(1);
+    if (j < d.cols) {
+      if (MODE == SYN_ID) src = idx[d.idx_off + d.rows + j];
+      else if (MODE == ADJ_ID) src = (long long)d.out_off + j;
+      else if (MODE == SYN_U) src = (long long)d.in_off + j;
+      else {
+        src = perm[d.out_off + j];
+        if (wts) w = wts[src];
+      }
+    }
 #pragma unroll
     for (int t = 0; t < RT; ++t)
 #pragma unroll
       for (int c = 0; c < W; ++c) {
         R v = R(0);
-        if (src >= 0 && t < nk) v = x[(src * xs_e + (long long)(k0 + t) * xs_k) * W + c];
-        xs[(t * ldt + j) * W + c] = v;
+        if (src >= 0 && t < nk) {
+          const long long a = (src * is_e + (long long)(k0 + t) * is_k) * W + c;
+          v = in0[a];
+          if (MODE == ADJ_ID && in1) v += in1[a];
+          v *= w;
+        }
+        xs[(t * ldx_max + j) * W + c] = v;
       }
   }
   __syncthreads();
 
+  if (MODE == ADJ_ID && it.start == 0) {  // identity part: out[skel_j] = z_j
+    for (int e = threadIdx.x; e < d.cols * nk; e += kThreads) {
+      const int j = e / nk, t = e % nk;
+      const long long dst = idx[d.idx_off + j];
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        out[(dst * os_e + (long long)(k0 + t) * os_k) * W + c] = xs[(t * ldx_max + j) * W + c];
+    }
+  }
+  if (it.count == 0) return;
+
+  if (bytes > 0 && !mbar_wait_bounded(bar, 0)) {
+    if (threadIdx.x == 0) atomicOr(status, 1u);
+    mbar_wait_bounded(bar, 0);  // let the copy land before the CTA releases shared memory
+    return;
+  }
+
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nvec = ldt / E;
-  for (int i = it.start + warp; i < it.start + it.count; i += kWarps) {
+  for (int ii = warp; ii < it.count; ii += kWarps) {
+    const int i = it.start + ii;
     R acc[RT][W];
 #pragma unroll
     for (int t = 0; t < RT; ++t)
 #pragma unroll
       for (int c = 0; c < W; ++c) acc[t][c] = R(0);
-    const R* row = data + (d.t_off + (long long)i * ldt) * W;
-#pragma unroll 4
+    const R* row = tile + (long long)ii * ldt * W;
     for (int v = lane; v < nvec; v += 32) {
-      const Vec16<R> tv = load16(row + v * NS);
+      const Vec16<R> tv = *reinterpret_cast<const Vec16<R>*>(row + v * NS);
 #pragma unroll
       for (int t = 0; t < RT; ++t) {
-        const Vec16<R> xv = *reinterpret_cast<const Vec16<R>*>(xs + (t * ldt + v * E) * W);
+        const Vec16<R> xv = *reinterpret_cast<const Vec16<R>*>(xs + (t * ldx_max + v * E) * W);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           if (C) {
@@ -137,158 +227,475 @@ k_synth(const R* __restrict__ data, const int* __restrict__ idx, const MhtBlockD
 #pragma unroll
           for (int c = 0; c < W; ++c) val[c] = acc[tt][c];
       long long dst;
-      if (U_STAGE) {
-        dst = (long long)perm[d.out_off + i];
+      if (MODE == SYN_ID) {
+        const long long s = idx[d.idx_off + i];
+#pragma unroll
+        for (int c = 0; c < W; ++c) val[c] += in0[(s * is_e + (long long)(k0 + t) * is_k) * W + c];
+        dst = (long long)d.out_off + i;
+      } else if (MODE == ADJ_ID) {
+        dst = idx[d.idx_off + d.cols + i];
+      } else if (MODE == SYN_U) {
+        dst = perm[d.out_off + i];
         if (wts) {
           const R w = wts[dst];
 #pragma unroll
           for (int c = 0; c < W; ++c) val[c] *= w;
         }
       } else {
-        const long long s = idx[d.idx_off + i];
-#pragma unroll
-        for (int c = 0; c < W; ++c) val[c] += x[(s * xs_e + (long long)(k0 + t) * xs_k) * W + c];
-        dst = (long long)(d.out_off + i);
+        dst = (long long)d.in_off + i;
       }
 #pragma unroll
-      for (int c = 0; c < W; ++c) y[(dst * ys_e + (long long)(k0 + t) * ys_k) * W + c] = val[c];
+      for (int c = 0; c < W; ++c) out[(dst * os_e + (long long)(k0 + t) * os_k) * W + c] = val[c];
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// Adjoint, one work item = (block, matrix columns [start, start+count)), RT RHS.
-//   ID stage:  z_i = z0[out_off + i] (+ z1[out_off + i]);  out[idx[i]] = z_i (first item);
-//              out[idx[r + j]] = sum_i conj(T~_ij) z_i;  out = sibling buffer `sib`
-//   U stage:   g_i = w[perm[out_off + i]] f[perm[out_off + i]];
-//              zL[in_off + j] = sum_i conj(U_ij) g_i
-template <class R, bool C, int RT, bool U_STAGE>
-__global__ void __launch_bounds__(kThreads)
-k_adjoint(const R* __restrict__ data, const int* __restrict__ idx, const MhtBlockDesc* __restrict__ desc,
-          const MhtItem* __restrict__ items, const int* __restrict__ perm, const R* __restrict__ wts,
-          const R* __restrict__ z0, const R* __restrict__ z1, long long zs_e, long long zs_k,
-          R* __restrict__ out0, R* __restrict__ out1, long long os_e, long long os_k, int nrhs) {
+// Persistent fused apply: every stage of one direction in a single launch.
+//
+// Three warp roles per CTA (one CTA per SM):
+//  * producer (warp 0, lane 0): takes work items from a global queue in dependency order,
+//    hands each to the gather warps through a small item queue, and streams its rows in
+//    chunks of at most one slot into a kSlots-deep shared-memory ring with 1-D TMA bulk
+//    copies (full/empty mbarriers).  Matrix tiles do not depend on earlier stages, so the
+//    producer runs ahead of the data dependencies and keeps HBM busy.
+//  * gather warps (kGatherWarps): one item ahead of the math, wait (bounded) until the
+//    blocks the item reads are complete, then stage its input vector, its identity terms
+//    and its output indices in one of two shared-memory buffers.
+//  * compute warps (kComputeWarps): for every chunk, reduce rows from shared memory and
+//    store results; the last warp to finish an item publishes it with a release fence and a
+//    per-block completion counter.  No CTA-wide barrier sits on this path.
+// Items are dequeued in increasing order and only wait on smaller items, so the oldest
+// unfinished item can always proceed: no deadlock, whether or not all CTAs are resident.
+// Intermediate vectors are read with L2-only loads (.cg), so a stale L1 line from a
+// neighbouring block is never used.  Every wait is bounded in time and watches the status
+// word, so an error ends the launch instead of hanging it.
+constexpr int kSlots = 4;
+constexpr int kItemQ = 4;
+constexpr int kComputeWarps = 16;
+constexpr int kGatherWarps = 4;
+constexpr int kFusedThreads = 32 * (1 + kGatherWarps + kComputeWarps);
+
+template <class R>
+struct FusedParams {
+  const R* data;
+  const int* idx;
+  const int* perm;
+  const R* wts;               // analysis / weighted-synthesis weights or null
+  const MhtBlockDesc* desc;   // [(L+2) * nb], stage-major, this direction
+  const int* targets;         // [(L+2) * nb] items per block
+  const MhtPItem* items;
+  int nitems;
+  const long long* vec_off;   // [L+2]
+  const R* cin;               // synthesis input c (column-major, ldc)
+  R* cout;                    // analysis output c
+  const R* fin;               // analysis input f (ldf)
+  R* fout;                    // synthesis output f
+  long long ldc, ldf;
+  R* Y;                       // synthesis level vectors
+  R* A0;                      // analysis sibling buffers
+  R* A1;
+  unsigned* done;             // [(L+2) * nb] completed items per block
+  unsigned* queue;
+  unsigned* status;
+  int L, nb, nrhs, slot_bytes, ldx, mrows;
+};
+
+struct ItemInfo {
+  MhtPItem it;
+  MhtBlockDesc d;
+};
+
+__device__ __forceinline__ void bar_gather() {
+  asm volatile("bar.sync 2, %0;" ::"n"(32 * kGatherWarps) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool aborted(const unsigned* status) {
+  return *reinterpret_cast<const volatile unsigned*>(status) != 0u;
+}
+
+// Wait until block `b` of stage `s` has all its items done; false on timeout / abort.
+__device__ __forceinline__ bool wait_block(const unsigned* done, const int* targets, int s, int nb, int b,
+                                           const unsigned* status) {
+  const unsigned* cnt = done + (long long)s * nb + b;
+  const unsigned tgt = unsigned(targets[(long long)s * nb + b]);
+  if (ld_acquire(cnt) >= tgt) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    __nanosleep(it < 64 ? 32 : 256);
+    if (ld_acquire(cnt) >= tgt) return true;
+    if ((it & 15) == 0 && (globaltimer_ns() - t0 > kWaitNs || aborted(status))) return false;
+  }
+}
+
+// Stage input / output bases and element strides (one complex value = one element).
+template <class R, int DIR, int W>
+struct StageIO {
+  const R* in0;
+  const R* in1;
+  R* out;
+  long long is_e, is_k, os_e, os_k;
+  __device__ __forceinline__ StageIO(const FusedParams<R>& p, int st, int blk) {
+    const int L = p.L;
+    const long long nr = p.nrhs;
+    in1 = nullptr;
+    is_e = nr; is_k = 1; os_e = nr; os_k = 1;
+    if (DIR == 0) {
+      in0 = st == 0 ? p.cin : p.Y + p.vec_off[st - 1] * nr * W;
+      if (st == 0) { is_e = 1; is_k = p.ldc; }
+      if (st == L + 1) { out = p.fout; os_e = 1; os_k = p.ldf; }
+      else out = p.Y + p.vec_off[st] * nr * W;
+    } else if (st == L + 1) {
+      in0 = p.fin; is_e = 1; is_k = p.ldf;
+      out = p.A0 + p.vec_off[L] * nr * W;
+    } else {
+      in0 = p.A0 + p.vec_off[st] * nr * W;
+      in1 = st == L ? nullptr : p.A1 + p.vec_off[st] * nr * W;
+      if (st == 0) { out = p.cout; os_e = 1; os_k = p.ldc; }
+      else out = (((blk >> (L - st)) & 1) ? p.A1 : p.A0) + p.vec_off[st - 1] * nr * W;
+    }
+  }
+};
+
+template <class R, bool C, int RT, int DIR>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_fused(FusedParams<R> p) {
   constexpr int W = C ? 2 : 1;
   constexpr int NS = 16 / sizeof(R);
   constexpr int E = NS / W;
-  constexpr int VPL = 2;                  // 16-byte vectors per lane per row
-  constexpr int NCOL = 32 * E * VPL;      // columns per item
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* red = reinterpret_cast<R*>(smem_raw);                 // [kWarps][NCOL][RT][W]
-  R* zs = red + kWarps * NCOL * RT * W;                    // [rows][RT][W]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + kSlots;
+  uint64_t* iq_full = empty + kSlots;
+  uint64_t* iq_empty = iq_full + kItemQ;
+  uint64_t* xready = iq_empty + kItemQ;
+  uint64_t* xfree = xready + 2;
+  int* item_cnt = reinterpret_cast<int*>(smem_raw + 192);   // [2]
+  int* iq = reinterpret_cast<int*>(smem_raw + 208);         // [kItemQ]
+  int4* meta = reinterpret_cast<int4*>(smem_raw + 256);     // [kSlots] {seq, row0, rows, flags}
+  ItemInfo* info = reinterpret_cast<ItemInfo*>(smem_raw + 320);  // [2]
+  unsigned char* slots = smem_raw + 512;
+  R* xs = reinterpret_cast<R*>(slots + size_t(kSlots) * p.slot_bytes);  // [2][RT][ldx][W]
+  R* ident = xs + size_t(2) * RT * p.ldx * W;                            // [2][RT][mrows][W]
+  int* oidx = reinterpret_cast<int*>(ident + size_t(2) * RT * p.mrows * W);  // [2][mrows]
+  const int es = W * sizeof(R);
+  const int L = p.L;
 
-  const MhtItem it = items[blockIdx.x];
-  const MhtBlockDesc d = desc[it.blk];
-  const int k0 = blockIdx.y * RT;
-  const int nk = min(RT, nrhs - k0);
-  R* out = it.sib ? out1 : out0;
-
-  for (int i = threadIdx.x; i < d.rows; i += kThreads) {
-    long long src;
-    R w = R(1);
-    if (U_STAGE) {
-      src = perm[d.out_off + i];
-      if (wts) w = wts[src];
-    } else {
-      src = d.out_off + i;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kSlots; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kComputeWarps);
     }
-#pragma unroll
-    for (int t = 0; t < RT; ++t)
-#pragma unroll
-      for (int c = 0; c < W; ++c) {
-        R v = R(0);
-        if (t < nk) {
-          const long long a = (src * zs_e + (long long)(k0 + t) * zs_k) * W + c;
-          v = z0[a];
-          if (!U_STAGE && z1) v += z1[a];
-          v *= w;
-        }
-        zs[(i * RT + t) * W + c] = v;
-      }
+    for (int i = 0; i < kItemQ; ++i) {
+      mbar_init(&iq_full[i], 1);
+      mbar_init(&iq_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&xready[i], 1);
+      mbar_init(&xfree[i], kComputeWarps);
+      item_cnt[i] = 0;
+    }
   }
   __syncthreads();
-
-  if (!U_STAGE && it.start == 0) {  // identity part of [I | T~] P^T
-    for (int e = threadIdx.x; e < d.rows * nk; e += kThreads) {
-      const int i = e / nk, t = e % nk;
-      const long long dst = idx[d.idx_off + i];
-#pragma unroll
-      for (int c = 0; c < W; ++c) out[(dst * os_e + (long long)(k0 + t) * os_k) * W + c] = zs[(i * RT + t) * W + c];
-    }
-  }
-  if (it.count == 0) return;
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nvec = d.ldt / E;
-  const int v0 = it.start / E;
-  R acc[VPL][E][RT][W];
-#pragma unroll
-  for (int u = 0; u < VPL; ++u)
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-#pragma unroll
-      for (int t = 0; t < RT; ++t)
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[u][e][t][c] = R(0);
-#pragma unroll 2
-  for (int i = warp; i < d.rows; i += kWarps) {
-    const R* row = data + (d.t_off + (long long)i * d.ldt) * W;
-    Vec16<R> tv[VPL];
-#pragma unroll
-    for (int u = 0; u < VPL; ++u) {
-      const int v = v0 + lane + 32 * u;
-      if (v < nvec) tv[u] = load16(row + v * NS);
-      else
-#pragma unroll
-        for (int q = 0; q < NS; ++q) tv[u].s[q] = R(0);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ producer
+    if (lane != 0) return;
+    long long issued = 0;
+    int k = 0;
+    bool ok = true;
+    for (;; ++k) {
+      if (aborted(p.status)) { ok = false; break; }
+      const int item = int(atomicAdd(p.queue, 1u));
+      if (item >= p.nitems) break;
+      if (!mbar_wait_bounded(&iq_empty[k % kItemQ], unsigned(((k / kItemQ) & 1) ^ 1), p.status)) {
+        atomicOr(p.status, 2u);
+        ok = false;
+        break;
+      }
+      iq[k % kItemQ] = item;
+      mbar_arrive(&iq_full[k % kItemQ]);
+      const MhtPItem it = p.items[item];
+      const MhtBlockDesc d = p.desc[(long long)it.stage * p.nb + it.blk];
+      const int rowbytes = d.ldt * es;
+      const int rpc = rowbytes > 0 ? max(1, p.slot_bytes / rowbytes) : max(1, it.count);
+      const int nch = it.count == 0 ? 1 : (it.count + rpc - 1) / rpc;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int s = int(issued % kSlots);
+        const unsigned ph = unsigned((issued / kSlots) & 1);
+        if (!mbar_wait_bounded(&empty[s], ph ^ 1u, p.status)) {
+          atomicOr(p.status, 2u);
+          ok = false;
+          break;
+        }
+        const int r0 = ch * rpc;
+        const int rows = it.count == 0 ? 0 : min(rpc, it.count - r0);
+        meta[s] = make_int4(k, r0, rows, (ch == 0 ? 1 : 0) | (ch == nch - 1 ? 2 : 0));
+        const unsigned bytes = unsigned(rows) * unsigned(rowbytes);
+        mbar_expect_tx(&full[s], bytes);
+        if (bytes > 0)
+          bulk_copy_g2s(slots + size_t(s) * p.slot_bytes, p.data + (d.t_off + (long long)(it.start + r0) * d.ldt) * W,
+                        bytes, &full[s]);
+        ++issued;
+      }
+      if (!ok) break;
     }
-#pragma unroll
-    for (int t = 0; t < RT; ++t) {
-      R zr = zs[(i * RT + t) * W], zi = C ? zs[(i * RT + t) * W + W - 1] : R(0);
-#pragma unroll
-      for (int u = 0; u < VPL; ++u)
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          if (C) {  // conj(a + ib) (zr + i zi)
-            const R a = tv[u].s[2 * e], b = tv[u].s[2 * e + 1];
-            acc[u][e][t][0] += a * zr + b * zi;
-            acc[u][e][t][W - 1] += a * zi - b * zr;
-          } else {
-            acc[u][e][t][0] += tv[u].s[e] * zr;
+    if (ok) {
+      // end markers for the gather and compute warps
+      const bool qok = mbar_wait_bounded(&iq_empty[k % kItemQ], unsigned(((k / kItemQ) & 1) ^ 1), p.status);
+      if (qok) {
+        iq[k % kItemQ] = -1;
+        mbar_arrive(&iq_full[k % kItemQ]);
+      }
+      const int s = int(issued % kSlots);
+      const unsigned ph = unsigned((issued / kSlots) & 1);
+      if (qok && mbar_wait_bounded(&empty[s], ph ^ 1u, p.status)) {
+        meta[s] = make_int4(-1, 0, 0, 0);
+        mbar_expect_tx(&full[s], 0);
+        return;  // the compute warps consume every earlier chunk before the marker
+      }
+      atomicOr(p.status, 2u);
+    }
+    // error path: every copy issued must land before the CTA's shared memory is released
+    for (long long j = (issued > kSlots ? issued - kSlots : 0ll); j < issued; ++j)
+      mbar_wait_bounded(&full[j % kSlots], unsigned((j / kSlots) & 1));
+    return;
+  }
+
+  if (warp <= kGatherWarps) {
+    // ------------------------------------------------------------------ gather warps
+    const int g = threadIdx.x - 32;
+    constexpr int NG = 32 * kGatherWarps;
+    volatile int* gflag = reinterpret_cast<volatile int*>(smem_raw + 224);  // broadcast slot
+    for (int k = 0;; ++k) {
+      const int b = k & 1;
+      // one thread waits for the next item and for its buffer; the group leaves together
+      if (g == 0) {
+        int item = -2;
+        if (mbar_wait_bounded(&iq_full[k % kItemQ], unsigned((k / kItemQ) & 1), p.status)) {
+          item = iq[k % kItemQ];
+          mbar_arrive(&iq_empty[k % kItemQ]);
+          if (item >= 0 && !mbar_wait_bounded(&xfree[b], unsigned(((k >> 1) & 1) ^ 1), p.status)) item = -2;
+        }
+        if (item == -2) atomicOr(p.status, 16u);
+        *gflag = item;
+      }
+      bar_gather();
+      const int item = *gflag;
+      bar_gather();
+      if (item < 0) return;
+      const MhtPItem it = p.items[item];
+      const MhtBlockDesc d = p.desc[(long long)it.stage * p.nb + it.blk];
+      const int st = it.stage;
+      const bool ustage = (st == L + 1);
+      if (g == 0) {
+        bool ok = true;
+        const int nbs = 1 << (L - min(st, L));
+        if (DIR == 0 && st >= 1 && st <= L) {
+          const int tau = it.blk / nbs, nu = it.blk % nbs, q = (tau >> 1) * (nbs << 1) + 2 * nu;
+          ok = wait_block(p.done, p.targets, st - 1, p.nb, q, p.status) &&
+               wait_block(p.done, p.targets, st - 1, p.nb, q + 1, p.status);
+        } else if (DIR == 0 && ustage) {
+          ok = wait_block(p.done, p.targets, L, p.nb, it.blk, p.status);
+        } else if (DIR == 1 && st == L) {
+          ok = wait_block(p.done, p.targets, L + 1, p.nb, it.blk, p.status);
+        } else if (DIR == 1 && st < L) {
+          const int tau = it.blk / nbs, nu = it.blk % nbs, nb1 = nbs >> 1;
+          ok = wait_block(p.done, p.targets, st + 1, p.nb, (2 * tau) * nb1 + (nu >> 1), p.status) &&
+               wait_block(p.done, p.targets, st + 1, p.nb, (2 * tau + 1) * nb1 + (nu >> 1), p.status);
+        }
+        if (!ok) atomicOr(p.status, 8u);
+        info[b].it = it;
+        info[b].d = d;
+      }
+      bar_gather();
+      const StageIO<R, DIR, W> io(p, st, it.blk);
+      const int nr = p.nrhs;
+      R* xb = xs + size_t(b) * RT * p.ldx * W;
+      // input vector (zero padding to ldt and beyond nrhs)
+#pragma unroll 4
+      for (int j = g; j < d.ldt; j += NG) {
+        long long src = -1;
+        R w = R(1);
+        if (j < d.cols) {
+          if (DIR == 0 && !ustage) src = p.idx[d.idx_off + d.rows + j];
+          else if (DIR == 1 && !ustage) src = (long long)d.out_off + j;
+          else if (DIR == 0) src = (long long)d.in_off + j;
+          else {
+            src = p.perm[d.out_off + j];
+            if (p.wts) w = p.wts[src];
           }
         }
+#pragma unroll
+        for (int t = 0; t < RT; ++t)
+#pragma unroll
+          for (int c = 0; c < W; ++c) {
+            R v = R(0);
+            if (src >= 0 && t < nr) {
+              const long long a = (src * io.is_e + (long long)t * io.is_k) * W + c;
+              v = __ldcg(io.in0 + a);
+              if (io.in1) v += __ldcg(io.in1 + a);
+              v *= w;
+            }
+            xb[(t * p.ldx + j) * W + c] = v;
+          }
+      }
+      // per-row identity terms, weights and output indices of this item
+      R* ib = ident + size_t(b) * RT * p.mrows * W;
+      int* ob = oidx + size_t(b) * p.mrows;
+#pragma unroll 4
+      for (int i = g; i < it.count; i += NG) {
+        const int row = it.start + i;
+        if (DIR == 0 && !ustage) {
+          const long long sidx = p.idx[d.idx_off + row];
+#pragma unroll
+          for (int t = 0; t < RT; ++t)
+#pragma unroll
+            for (int c = 0; c < W; ++c)
+              ib[(t * p.mrows + i) * W + c] =
+                  t < nr ? __ldcg(io.in0 + (sidx * io.is_e + (long long)t * io.is_k) * W + c) : R(0);
+        } else if (DIR == 1 && !ustage) {
+          ob[i] = p.idx[d.idx_off + d.cols + row];
+        } else if (DIR == 0) {
+          const int dst = p.perm[d.out_off + row];
+          ob[i] = dst;
+          ib[i * W] = p.wts ? p.wts[dst] : R(1);
+        }
+      }
+      if (DIR == 1 && !ustage && it.start == 0) {  // identity part: out[skel_j] = z_j
+        bar_gather();  // the staged vector is complete (entries come from other threads)
+        for (int e = g; e < d.cols * nr; e += NG) {
+          const int j = e / nr, t = e % nr;
+          const long long dst = p.idx[d.idx_off + j];
+#pragma unroll
+          for (int c = 0; c < W; ++c)
+            io.out[(dst * io.os_e + (long long)t * io.os_k) * W + c] = xb[(t * p.ldx + j) * W + c];
+        }
+        __threadfence();  // visible before the compute warps publish the item
+      }
+      bar_gather();
+      if (g == 0) mbar_arrive(&xready[b]);
     }
   }
-#pragma unroll
-  for (int u = 0; u < VPL; ++u)
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int col = (lane + 32 * u) * E + e;
+
+  // -------------------------------------------------------------------- compute warps
+  const int cw = warp - 1 - kGatherWarps;
+  for (long long iter = 0;; ++iter) {
+    const int s = int(iter % kSlots);
+    const unsigned ph = unsigned((iter / kSlots) & 1);
+    // lane 0 waits for the chunk (and, at an item's first chunk, for its staged vectors);
+    // the whole warp follows its verdict
+    int okw = 1;
+    if (lane == 0) {
+      okw = mbar_wait_bounded(&full[s], ph, p.status) ? 1 : 0;
+      if (okw) {
+        const int4 m0 = meta[s];
+        if (m0.x >= 0 && (m0.w & 1) && !mbar_wait_bounded(&xready[m0.x & 1], unsigned((m0.x >> 1) & 1), p.status))
+          okw = 0;
+      }
+      if (!okw) atomicOr(p.status, 4u);
+    }
+    okw = __shfl_sync(0xffffffffu, okw, 0);
+    if (!okw) return;
+    const int4 m = meta[s];
+    if (m.x < 0) return;
+    const int k = m.x, b = k & 1;
+    const MhtPItem it = info[b].it;
+    const MhtBlockDesc d = info[b].d;
+    const int st = it.stage;
+    const bool ustage = (st == L + 1);
+    const StageIO<R, DIR, W> io(p, st, it.blk);
+    const int nr = p.nrhs;
+    const R* xb = xs + size_t(b) * RT * p.ldx * W;
+    const R* ib = ident + size_t(b) * RT * p.mrows * W;
+    const int* ob = oidx + size_t(b) * p.mrows;
+    const R* tile = reinterpret_cast<const R*>(slots + size_t(s) * p.slot_bytes);
+    const int nvec = d.ldt / E;
+    for (int ii = cw; ii < m.z; ii += kComputeWarps) {
+      const int il = m.y + ii;  // row within the item
+      R acc[RT][W];
 #pragma unroll
       for (int t = 0; t < RT; ++t)
 #pragma unroll
-        for (int c = 0; c < W; ++c) red[((warp * NCOL + col) * RT + t) * W + c] = acc[u][e][t][c];
+        for (int c = 0; c < W; ++c) acc[t][c] = R(0);
+      const R* row = tile + (long long)ii * d.ldt * W;
+      for (int v = lane; v < nvec; v += 32) {
+        const Vec16<R> tv = *reinterpret_cast<const Vec16<R>*>(row + v * NS);
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+          const Vec16<R> xv = *reinterpret_cast<const Vec16<R>*>(xb + (t * p.ldx + v * E) * W);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            if (C) {
+              const R a = tv.s[2 * e], bb = tv.s[2 * e + 1];
+              const R xr = xv.s[2 * e], xi = xv.s[2 * e + 1];
+              acc[t][0] += a * xr - bb * xi;
+              acc[t][W - 1] += a * xi + bb * xr;
+            } else {
+              acc[t][0] += tv.s[e] * xv.s[e];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < RT; ++t)
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[t][c] = warp_sum(acc[t][c]);
+      if (lane < nr && lane < RT) {
+        const int t = lane;
+        R val[W];
+#pragma unroll
+        for (int tt = 0; tt < RT; ++tt)
+          if (tt == t)
+#pragma unroll
+            for (int c = 0; c < W; ++c) val[c] = acc[tt][c];
+        long long dst;
+        if (DIR == 0 && !ustage) {
+#pragma unroll
+          for (int c = 0; c < W; ++c) val[c] += ib[(t * p.mrows + il) * W + c];
+          dst = (long long)d.out_off + it.start + il;
+        } else if (DIR == 1 && !ustage) {
+          dst = ob[il];
+        } else if (DIR == 0) {
+          dst = ob[il];
+          const R w = ib[il * W];
+#pragma unroll
+          for (int c = 0; c < W; ++c) val[c] *= w;
+        } else {
+          dst = (long long)d.in_off + it.start + il;
+        }
+#pragma unroll
+        for (int c = 0; c < W; ++c) io.out[(dst * io.os_e + (long long)t * io.os_k) * W + c] = val[c];
+      }
     }
-  __syncthreads();
-  for (int e = threadIdx.x; e < it.count * nk; e += kThreads) {
-    const int col = e / nk, t = e % nk;
-    const int j = it.start + col;
-    R s[W];
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-      s[c] = R(0);
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) s[c] += red[((w * NCOL + col) * RT + t) * W + c];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (m.w & 2) {  // this warp is done with the item
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        if (atomicAdd(&item_cnt[b], 1) == kComputeWarps - 1) {
+          item_cnt[b] = 0;
+          __threadfence();
+          atomicAdd(p.done + (long long)st * p.nb + it.blk, 1u);
+        }
+        mbar_arrive(&xfree[b]);
+      }
     }
-    const long long dst = U_STAGE ? (long long)(d.in_off + j) : (long long)idx[d.idx_off + d.rows + j];
-#pragma unroll
-    for (int c = 0; c < W; ++c) out[(dst * os_e + (long long)(k0 + t) * os_k) * W + c] = s[c];
   }
 }
 
-// ---------------------------------------------------------------------------------------
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// Stage timing (mht_plan_profile): CUDA events around each launch.
 struct Profiler {
   struct Rec {
     int dir, stage;
@@ -352,7 +759,7 @@ int profiler_read(Profiler* p, int direction, int nstages, double* ms, int64_t* 
 
 namespace {
 
-struct StageTimer {  // records events around one launch when profiling is enabled
+struct StageTimer {
   Profiler* p;
   int dir, stage;
   cudaStream_t s;
@@ -381,97 +788,65 @@ struct Ctx {
   std::string& err;
 };
 
-template <class R>
-const R* data_ptr(const Ctx& c) { return reinterpret_cast<const R*>(c.d.base + c.P.data_off); }
-const int* idx_ptr(const Ctx& c) { return reinterpret_cast<const int*>(c.d.base + c.P.index_off); }
-const int* perm_ptr(const Ctx& c) { return reinterpret_cast<const int*>(c.d.base + c.P.perm_off); }
-const MhtBlockDesc* desc_ptr(const Ctx& c, int s) {
-  return reinterpret_cast<const MhtBlockDesc*>(c.d.base + c.P.st[s].desc_off);
-}
-const MhtItem* items_ptr(const Ctx& c, int s, bool syn) {
-  return reinterpret_cast<const MhtItem*>(c.d.base + (syn ? c.P.st[s].items_syn_off : c.P.st[s].items_adj_off));
-}
-
 int check(cudaError_t e, std::string& err, const char* what) {
   if (e == cudaSuccess) return 0;
   err = std::string(what) + ": " + cudaGetErrorString(e);
   return MHT_ERR_CUDA;
 }
 
+// Workspace level vectors: region 0 = Y (synthesis), 1 = A0, 2 = A1 (adjoint siblings);
+// level l of a region starts at vec_off[l] entries (times nrhs).
+void* lvl(const Ctx& c, int region, int l) {
+  return c.d.ws + region * c.P.ws_vec_bytes(c.d.max_nrhs) + size_t(c.P.vec_off[l]) * c.nrhs * c.P.elem_bytes;
+}
+unsigned* status_ptr(const Ctx& c) {
+  return reinterpret_cast<unsigned*>(c.d.ws + c.P.status_offset(c.d.max_nrhs, c.F.n, c.F.m));
+}
 
-template <class R, bool C, int RT, bool U>
-int launch_synth(const Ctx& c, int s, const void* x, long long xs_e, long long xs_k, void* y,
-                 long long ys_e, long long ys_k, const void* w = nullptr) {
+size_t stage_smem(const Packed& P, const Stage& S, int dir, int rt) {
+  const size_t tile = (S.dir[dir].max_tile_bytes + 127) / 128 * 128;
+  return 128 + tile + size_t(std::max<int64_t>(S.dir[dir].max_ld, 1)) * rt * P.elem_bytes;
+}
+
+template <class R, bool C, int RT, int MODE>
+int launch(const Ctx& c, int s, const void* in0, const void* in1, long long is_e, long long is_k, void* out0,
+           void* out1, long long os_e, long long os_k, const void* w) {
+  const int dir = (MODE == ADJ_ID || MODE == ADJ_U) ? 1 : 0;
   const Stage& S = c.P.st[s];
-  if (S.nitems_syn == 0) return 0;
-  constexpr int W = C ? 2 : 1;
-  int64_t maxldt = 0;
-  {
-    constexpr int E = 16 / sizeof(R) / W;
-    maxldt = (S.max_cols + E - 1) / E * E;
-  }
-  const size_t smem = size_t(std::max<int64_t>(maxldt, 1)) * RT * W * sizeof(R);
-  auto kern = k_synth<R, C, RT, U>;
+  const StageDir& D = S.dir[dir];
+  if (D.nitems == 0) return 0;
+  const size_t smem = stage_smem(c.P, S, dir, RT);
   if (smem > 227 * 1024) {
-    c.err = "synthesis stage needs too much shared memory for this RHS tile";
+    c.err = "a stage needs more shared memory than an SM has for this RHS tile";
     return MHT_ERR_UNSUPPORTED;
   }
-  if (smem > 48 * 1024) {
-    if (int rc = check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), c.err, "smem attr")) return rc;
-  }
-  dim3 grid(unsigned(S.nitems_syn), unsigned((c.nrhs + RT - 1) / RT));
-  StageTimer timer(c.d.prof, 0, s, c.s);
-  kern<<<grid, kThreads, smem, c.s>>>(data_ptr<R>(c), idx_ptr(c), desc_ptr(c, s), items_ptr(c, s, true), perm_ptr(c),
-                                      static_cast<const R*>(w), static_cast<const R*>(x), xs_e, xs_k,
-                                      static_cast<R*>(y), ys_e, ys_k,
-                                      int(c.nrhs));
-  return check(cudaGetLastError(), c.err, "synthesis launch");
+  auto kern = k_rowdot<R, C, RT, MODE>;
+  if (smem > 48 * 1024)
+    if (int rc = check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), c.err,
+                       "shared memory attribute"))
+      return rc;
+  const uint8_t* base = c.d.base;
+  dim3 grid(unsigned(D.nitems), unsigned((c.nrhs + RT - 1) / RT));
+  StageTimer timer(c.d.prof, dir, s, c.s);
+  kern<<<grid, kThreads, smem, c.s>>>(
+      reinterpret_cast<const R*>(base + c.P.data_off), reinterpret_cast<const int*>(base + c.P.index_off),
+      reinterpret_cast<const MhtBlockDesc*>(base + D.desc_off), reinterpret_cast<const MhtItem*>(base + D.items_off),
+      reinterpret_cast<const int*>(base + c.P.perm_off), static_cast<const R*>(w), static_cast<const R*>(in0),
+      static_cast<const R*>(in1), is_e, is_k, static_cast<R*>(out0), static_cast<R*>(out1), os_e, os_k,
+      int(c.nrhs), int(D.max_tile_bytes), int(std::max<int64_t>(D.max_ld, 1)), status_ptr(c));
+  return check(cudaGetLastError(), c.err, "apply launch");
 }
-
-template <class R, bool C, int RT, bool U>
-int launch_adjoint(const Ctx& c, int s, const void* z0, const void* z1, long long zs_e, long long zs_k,
-                   void* o0, void* o1, long long os_e, long long os_k, const void* w) {
-  const Stage& S = c.P.st[s];
-  if (S.nitems_adj == 0) return 0;
-  constexpr int W = C ? 2 : 1;
-  constexpr int E = 16 / sizeof(R) / W;
-  constexpr int NCOL = 32 * E * 2;
-  const size_t smem = (size_t(kWarps) * NCOL * RT * W + size_t(std::max<int64_t>(S.max_rows, 1)) * RT * W) * sizeof(R);
-  auto kern = k_adjoint<R, C, RT, U>;
-  if (smem > 227 * 1024) {
-    c.err = "adjoint stage needs too much shared memory for this RHS tile";
-    return MHT_ERR_UNSUPPORTED;
-  }
-  if (smem > 48 * 1024) {
-    if (int rc = check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), c.err, "smem attr")) return rc;
-  }
-  dim3 grid(unsigned(S.nitems_adj), unsigned((c.nrhs + RT - 1) / RT));
-  StageTimer timer(c.d.prof, 1, s, c.s);
-  kern<<<grid, kThreads, smem, c.s>>>(data_ptr<R>(c), idx_ptr(c), desc_ptr(c, s), items_ptr(c, s, false), perm_ptr(c),
-                                      static_cast<const R*>(w), static_cast<const R*>(z0), static_cast<const R*>(z1),
-                                      zs_e, zs_k, static_cast<R*>(o0), static_cast<R*>(o1), os_e, os_k, int(c.nrhs));
-  return check(cudaGetLastError(), c.err, "adjoint launch");
-}
-
-size_t vec_bytes(const Ctx& c) {
-  return (size_t(std::max<int64_t>(c.P.vec_entries, 1)) * c.d.max_nrhs * c.P.elem_bytes + 255) / 256 * 256;
-}
-void* wsbuf(const Ctx& c, int i) { return c.d.ws + i * vec_bytes(c); }
 
 template <class R, bool C, int RT>
 int synth_impl(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool weighted) {
   const int L = c.F.L;
   const long long nr = c.nrhs;
-  int cur = 0;
-  int rc = launch_synth<R, C, RT, false>(c, 0, cin, 1, ldc, wsbuf(c, cur), nr, 1);
+  int rc = launch<R, C, RT, SYN_ID>(c, 0, cin, nullptr, 1, ldc, lvl(c, 0, 0), nullptr, nr, 1, nullptr);
+  for (int l = 1; l <= L && !rc; ++l)
+    rc = launch<R, C, RT, SYN_ID>(c, l, lvl(c, 0, l - 1), nullptr, nr, 1, lvl(c, 0, l), nullptr, nr, 1, nullptr);
   if (rc) return rc;
-  for (int l = 1; l <= L; ++l) {
-    rc = launch_synth<R, C, RT, false>(c, l, wsbuf(c, cur), nr, 1, wsbuf(c, 1 - cur), nr, 1);
-    if (rc) return rc;
-    cur = 1 - cur;
-  }
   const void* w = weighted ? (const void*)(c.d.base + c.P.weights_off) : nullptr;
-  return launch_synth<R, C, RT, true>(c, L + 1, wsbuf(c, cur), nr, 1, f, 1, ldf, w);
+  return launch<R, C, RT, SYN_U>(c, L + 1, lvl(c, 0, L), nullptr, nr, 1, f, nullptr, 1, ldf, w);
 }
 
 template <class R, bool C, int RT>
@@ -479,47 +854,128 @@ int adjoint_impl(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t l
   const int L = c.F.L;
   const long long nr = c.nrhs;
   const void* w = weighted ? (const void*)(c.d.base + c.P.weights_off) : nullptr;
-  // U^H: f -> z_L (buffer 0)
-  int rc = launch_adjoint<R, C, RT, true>(c, L + 1, f, nullptr, 1, ldf, wsbuf(c, 0), wsbuf(c, 0), nr, 1, w);
+  // U^H: f -> z_L (region A0, level L)
+  int rc = launch<R, C, RT, ADJ_U>(c, L + 1, f, nullptr, 1, ldf, lvl(c, 1, L), nullptr, nr, 1, w);
+  for (int l = L; l >= 1 && !rc; --l)
+    rc = launch<R, C, RT, ADJ_ID>(c, l, lvl(c, 1, l), l == L ? nullptr : lvl(c, 2, l), nr, 1, lvl(c, 1, l - 1),
+                                  lvl(c, 2, l - 1), nr, 1, nullptr);
   if (rc) return rc;
-  const void* z0 = wsbuf(c, 0);
-  const void* z1 = nullptr;
-  int pair = 0;  // output pairs alternate (1,2) and (3,0)
-  for (int l = L; l >= 1; --l) {
-    void* o0 = wsbuf(c, pair == 0 ? 1 : 3);
-    void* o1 = wsbuf(c, pair == 0 ? 2 : 0);
-    rc = launch_adjoint<R, C, RT, false>(c, l, z0, z1, nr, 1, o0, o1, nr, 1, nullptr);
-    if (rc) return rc;
-    z0 = o0;
-    z1 = o1;
-    pair = 1 - pair;
-  }
-  return launch_adjoint<R, C, RT, false>(c, 0, z0, z1, nr, 1, cout, cout, 1, ldc, nullptr);
+  return launch<R, C, RT, ADJ_ID>(c, 0, lvl(c, 1, 0), L == 0 ? nullptr : lvl(c, 2, 0), nr, 1, cout, cout, 1, ldc,
+                                  nullptr);
 }
 
-// Largest RHS tile (8, 4, 2, 1) whose shared memory fits every stage.
-template <class R, bool C>
-int pick_rt(const Ctx& c, bool synth) {
-  constexpr int W = C ? 2 : 1;
-  constexpr int E = 16 / sizeof(R) / W;
-  constexpr int NCOL = 32 * E * 2;
-  int64_t maxcols = 1, maxrows = 1;
-  for (const Stage& s : c.P.st) {
-    maxcols = std::max<int64_t>(maxcols, (s.max_cols + E - 1) / E * E);
-    maxrows = std::max<int64_t>(maxrows, s.max_rows);
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
   }
+  return n;
+}
+
+size_t fused_smem(const Packed& P, int dir, int rt) {
+  const FusedDir& FD = P.fused[dir];
+  const size_t mrows = size_t(std::max<int64_t>(FD.max_item_rows, 1));
+  return 512 + size_t(kSlots) * FD.slot_bytes + 2 * size_t(std::max<int64_t>(FD.max_ld, 1)) * rt * P.elem_bytes +
+         2 * mrows * rt * P.elem_bytes + 2 * mrows * sizeof(int);
+}
+
+unsigned* counters(const Ctx& c, int dir) {
+  unsigned* base = reinterpret_cast<unsigned*>(c.d.ws + c.P.ws_counters_offset(c.d.max_nrhs, c.F.n, c.F.m));
+  return base + size_t(dir) * (size_t(c.P.L + 2) * c.P.nb + 1);
+}
+
+// One launch for every stage of a direction (returns -1 when the shared memory does not fit).
+template <class R, bool C, int RT, int DIR>
+int fused_launch(const Ctx& c, const void* in, long long ld_in, void* out, long long ld_out, bool weighted) {
+  const FusedDir& FD = c.P.fused[DIR];
+  const size_t smem = fused_smem(c.P, DIR, RT);
+  if (smem > 227 * 1024) return -1;
+  auto kern = k_fused<R, C, RT, DIR>;
+  if (int rc = check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), c.err,
+                     "shared memory attribute"))
+    return rc;
+  const size_t ncnt = size_t(c.P.L + 2) * c.P.nb + 1;
+  unsigned* cnt = counters(c, DIR);
+  if (int rc = check(cudaMemsetAsync(cnt, 0, ncnt * sizeof(unsigned), c.s), c.err, "counter reset")) return rc;
+  if (FD.nitems == 0) return 0;
+  const uint8_t* base = c.d.base;
+  FusedParams<R> p;
+  p.data = reinterpret_cast<const R*>(base + c.P.data_off);
+  p.idx = reinterpret_cast<const int*>(base + c.P.index_off);
+  p.perm = reinterpret_cast<const int*>(base + c.P.perm_off);
+  p.wts = weighted ? reinterpret_cast<const R*>(base + c.P.weights_off) : nullptr;
+  p.desc = reinterpret_cast<const MhtBlockDesc*>(base + FD.desc_all_off);
+  p.targets = reinterpret_cast<const int*>(base + FD.targets_off);
+  p.items = reinterpret_cast<const MhtPItem*>(base + FD.items_off);
+  p.nitems = int(FD.nitems);
+  p.vec_off = reinterpret_cast<const long long*>(base + c.P.vecoff_off);
+  p.cin = DIR == 0 ? static_cast<const R*>(in) : nullptr;
+  p.cout = DIR == 1 ? static_cast<R*>(out) : nullptr;
+  p.fin = DIR == 1 ? static_cast<const R*>(in) : nullptr;
+  p.fout = DIR == 0 ? static_cast<R*>(out) : nullptr;
+  p.ldc = DIR == 0 ? ld_in : ld_out;
+  p.ldf = DIR == 0 ? ld_out : ld_in;
+  p.Y = static_cast<R*>(lvl(c, 0, 0));
+  p.A0 = static_cast<R*>(lvl(c, 1, 0));
+  p.A1 = static_cast<R*>(lvl(c, 2, 0));
+  p.done = cnt;
+  p.queue = cnt + ncnt - 1;
+  p.status = status_ptr(c);
+  p.L = c.P.L;
+  p.nb = int(c.P.nb);
+  p.nrhs = int(c.nrhs);
+  p.slot_bytes = int(FD.slot_bytes);
+  p.ldx = int(std::max<int64_t>(FD.max_ld, 1));
+  p.mrows = int(std::max<int64_t>(FD.max_item_rows, 1));
+  const int grid = int(std::min<int64_t>(num_sms(), FD.nitems));
+  StageTimer timer(c.d.prof, DIR, c.P.L + 2, c.s);
+  kern<<<grid, kFusedThreads, smem, c.s>>>(p);
+  return check(cudaGetLastError(), c.err, "fused apply launch");
+}
+
+// Smallest RHS tile (1, 2, 4, 8) that covers nrhs in one fused launch, or 0 if none fits.
+int fused_rt(const Ctx& c, int dir) {
+  if (c.d.path == 1 || c.nrhs > 8) return 0;
+  for (int rt = 1; rt <= 8; rt *= 2)
+    if (rt >= c.nrhs) return fused_smem(c.P, dir, rt) <= 227 * 1024 ? rt : 0;
+  return 0;
+}
+
+template <class R, bool C, int DIR>
+int fused_dispatch(const Ctx& c, int rt, const void* in, long long ld_in, void* out, long long ld_out, bool wt) {
+  switch (rt) {
+    case 1: return fused_launch<R, C, 1, DIR>(c, in, ld_in, out, ld_out, wt);
+    case 2: return fused_launch<R, C, 2, DIR>(c, in, ld_in, out, ld_out, wt);
+    case 4: return fused_launch<R, C, 4, DIR>(c, in, ld_in, out, ld_out, wt);
+    default: return fused_launch<R, C, 8, DIR>(c, in, ld_in, out, ld_out, wt);
+  }
+}
+
+// Largest RHS tile (8, 4, 2, 1), at most nrhs, whose shared memory fits every stage.
+int pick_rt(const Ctx& c, int dir) {
   for (int rt = 8; rt >= 1; rt /= 2) {
     if (rt > 1 && c.nrhs < rt) continue;
-    const size_t need = synth ? size_t(maxcols) * rt * W * sizeof(R)
-                              : (size_t(kWarps) * NCOL + size_t(maxrows)) * rt * W * sizeof(R);
-    if (need <= 227 * 1024) return rt;
+    bool ok = true;
+    for (const Stage& s : c.P.st) ok = ok && stage_smem(c.P, s, dir, rt) <= 227 * 1024;
+    if (ok) return rt;
   }
   return 1;
 }
 
 template <class R, bool C>
 int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool wt) {
-  switch (pick_rt<R, C>(c, true)) {
+  if (const int rt = fused_rt(c, 0)) {
+    const int rc = fused_dispatch<R, C, 0>(c, rt, cin, ldc, f, ldf, wt);
+    if (rc >= 0) return rc;
+  }
+  if (c.d.path == 2) {
+    c.err = "the fused apply does not fit this plan / RHS count";
+    return MHT_ERR_UNSUPPORTED;
+  }
+  switch (pick_rt(c, 0)) {
     case 8: return synth_impl<R, C, 8>(c, cin, ldc, f, ldf, wt);
     case 4: return synth_impl<R, C, 4>(c, cin, ldc, f, ldf, wt);
     case 2: return synth_impl<R, C, 2>(c, cin, ldc, f, ldf, wt);
@@ -528,7 +984,15 @@ int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t 
 }
 template <class R, bool C>
 int adjoint_dispatch(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t ldc, bool wt) {
-  switch (pick_rt<R, C>(c, false)) {
+  if (const int rt = fused_rt(c, 1)) {
+    const int rc = fused_dispatch<R, C, 1>(c, rt, f, ldf, cout, ldc, wt);
+    if (rc >= 0) return rc;
+  }
+  if (c.d.path == 2) {
+    c.err = "the fused apply does not fit this plan / RHS count";
+    return MHT_ERR_UNSUPPORTED;
+  }
+  switch (pick_rt(c, 1)) {
     case 8: return adjoint_impl<R, C, 8>(c, f, ldf, cout, ldc, wt);
     case 4: return adjoint_impl<R, C, 4>(c, f, ldf, cout, ldc, wt);
     case 2: return adjoint_impl<R, C, 2>(c, f, ldf, cout, ldc, wt);
@@ -536,32 +1000,39 @@ int adjoint_dispatch(const Ctx& c, const void* f, int64_t ldf, void* cout, int64
   }
 }
 
-
 }  // namespace
 
-int apply_synthesize(const Factorization& F, const Packed& P, const DeviceView& d, const void* c,
-                     int64_t ldc, void* f, int64_t ldf, int64_t nrhs, bool wt, mht_apply_mode mode,
-                     void* stream, std::string& err) {
+int apply_synthesize(const Factorization& F, const Packed& P, const DeviceView& d, const void* c, int64_t ldc,
+                     void* f, int64_t ldf, int64_t nrhs, bool wt, mht_apply_mode mode, void* stream,
+                     std::string& err) {
   Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err};
   (void)mode;
-  if (P.fp64) return P.cplx ? synth_dispatch<double, true>(x, c, ldc, f, ldf, wt) : synth_dispatch<double, false>(x, c, ldc, f, ldf, wt);
+  if (P.fp64)
+    return P.cplx ? synth_dispatch<double, true>(x, c, ldc, f, ldf, wt)
+                  : synth_dispatch<double, false>(x, c, ldc, f, ldf, wt);
   return P.cplx ? synth_dispatch<float, true>(x, c, ldc, f, ldf, wt) : synth_dispatch<float, false>(x, c, ldc, f, ldf, wt);
 }
 
-int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, const void* f,
-                  int64_t ldf, void* c, int64_t ldc, int64_t nrhs, bool weighted,
-                  mht_apply_mode mode, void* stream, std::string& err) {
+int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, const void* f, int64_t ldf, void* c,
+                  int64_t ldc, int64_t nrhs, bool weighted, mht_apply_mode mode, void* stream, std::string& err) {
   Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err};
   (void)mode;
-  if (P.fp64) return P.cplx ? adjoint_dispatch<double, true>(x, f, ldf, c, ldc, weighted) : adjoint_dispatch<double, false>(x, f, ldf, c, ldc, weighted);
-  return P.cplx ? adjoint_dispatch<float, true>(x, f, ldf, c, ldc, weighted) : adjoint_dispatch<float, false>(x, f, ldf, c, ldc, weighted);
+  if (P.fp64)
+    return P.cplx ? adjoint_dispatch<double, true>(x, f, ldf, c, ldc, weighted)
+                  : adjoint_dispatch<double, false>(x, f, ldf, c, ldc, weighted);
+  return P.cplx ? adjoint_dispatch<float, true>(x, f, ldf, c, ldc, weighted)
+                : adjoint_dispatch<float, false>(x, f, ldf, c, ldc, weighted);
 }
 
-int64_t apply_launches(const Packed& P, int64_t nrhs, mht_apply_mode mode) {
+int64_t apply_launches(const Packed& P, int64_t nrhs, mht_apply_mode mode, int path) {
   (void)mode;
-  (void)nrhs;
+  if (path != 1 && nrhs <= 8) {
+    int rt = 1;
+    while (rt < nrhs) rt *= 2;
+    if (fused_smem(P, 0, rt) <= 227 * 1024) return P.fused[0].nitems > 0 ? 1 : 0;
+  }
   int64_t n = 0;
-  for (const Stage& s : P.st) n += (s.nitems_syn > 0) ? 1 : 0;
+  for (const Stage& s : P.st) n += (s.dir[0].nitems > 0) ? 1 : 0;
   return n;
 }
 
@@ -579,6 +1050,15 @@ int device_copy_async(void* dst, const void* src, size_t bytes, int kind, void* 
 
 int device_sync(void* stream, std::string& err) {
   return check(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), err, "stream sync");
+}
+
+int device_status(void* status_dev, void* stream, unsigned* flags, std::string& err) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = check(cudaMemcpyAsync(flags, status_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s), err,
+                     "status read"))
+    return rc;
+  if (int rc = check(cudaMemsetAsync(status_dev, 0, sizeof(unsigned), s), err, "status clear")) return rc;
+  return check(cudaStreamSynchronize(s), err, "status sync");
 }
 
 }  // namespace mht

@@ -203,7 +203,7 @@ mht_status mht_plan_level_info(const mht_plan* plan, int32_t level, mht_level_in
     info->rank_median = r[r.size() / 2];
     for (int64_t v : r) info->rank_sum += v;
     info->transfer_entries = plan->P.st[level].t_entries;
-    info->bytes = plan->P.st[level].data_bytes;
+    info->bytes = plan->P.st[level].dir[0].data_bytes + plan->P.st[level].dir[1].data_bytes;
     info->algorithmic_bytes = plan->P.st[level].alg_bytes;
     return MHT_OK;
   });
@@ -236,6 +236,10 @@ mht_status mht_plan_bind_device(mht_plan* plan, void* factor_dev, size_t factor_
     plan->dev.ws = static_cast<uint8_t*>(workspace_dev);
     plan->dev.ws_bytes = workspace_bytes;
     plan->dev.max_nrhs = max_nrhs;
+    unsigned flags = 0;
+    if (int rc = mht::device_status(plan->dev.ws + plan->P.status_offset(max_nrhs, plan->F.n, plan->F.m), stream,
+                                    &flags, err))
+      return set_error(mht_status(rc), err);
     plan->bound = true;
     return MHT_OK;
   });
@@ -283,12 +287,10 @@ mht_status mht_analyze(mht_plan* plan, const void* f_dev, int64_t ldf, void* c_d
   });
 }
 
-static void* staging(mht_plan* plan, int which, int64_t nrhs) {
+static void* staging(mht_plan* plan, int which) {
   const mht::Packed& P = plan->P;
-  const size_t vec = (size_t(std::max<int64_t>(P.vec_entries, 1)) * plan->dev.max_nrhs * P.elem_bytes + 255) / 256 * 256;
   const size_t sc = (size_t(plan->F.m) * plan->dev.max_nrhs * P.elem_bytes + 255) / 256 * 256;
-  (void)nrhs;
-  return plan->dev.ws + 4 * vec + (which == 0 ? 0 : sc);
+  return plan->dev.ws + 3 * P.ws_vec_bytes(plan->dev.max_nrhs) + (which == 0 ? 0 : sc);
 }
 
 static mht_status host_transform(mht_plan* plan, bool synth, const void* in, int64_t ldi, void* out, int64_t ldo,
@@ -296,8 +298,8 @@ static mht_status host_transform(mht_plan* plan, bool synth, const void* in, int
   const int64_t nin = synth ? plan->F.m : plan->F.n, nout = synth ? plan->F.n : plan->F.m;
   check_apply(plan, in, ldi, nin, out, ldo, nout, nrhs);
   const size_t es = size_t(plan->P.elem_bytes);
-  uint8_t* din = static_cast<uint8_t*>(staging(plan, synth ? 0 : 1, nrhs));
-  uint8_t* dout = static_cast<uint8_t*>(staging(plan, synth ? 1 : 0, nrhs));
+  uint8_t* din = static_cast<uint8_t*>(staging(plan, synth ? 0 : 1));
+  uint8_t* dout = static_cast<uint8_t*>(staging(plan, synth ? 1 : 0));
   std::string err;
   int rc = 0;
   for (int64_t k = 0; k < nrhs && !rc; ++k)
@@ -328,7 +330,30 @@ mht_status mht_analyze_host(mht_plan* plan, const void* f_host, int64_t ldf, voi
 mht_status mht_apply_launch_count(const mht_plan* plan, int64_t nrhs, int64_t* launches) {
   return guarded([&]() -> mht_status {
     if (!plan || !launches || nrhs < 1) mht::fail(MHT_ERR_INVALID_ARG, "bad argument");
-    *launches = mht::apply_launches(plan->P, nrhs, plan->mode);
+    *launches = mht::apply_launches(plan->P, nrhs, plan->mode, plan->dev.path);
+    return MHT_OK;
+  });
+}
+
+mht_status mht_plan_check(mht_plan* plan, void* stream, int32_t* flags) {
+  return guarded([&]() -> mht_status {
+    if (!plan || !flags) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    if (!plan->bound) mht::fail(MHT_ERR_NOT_BOUND, "plan has no bound device buffers");
+    std::string err;
+    unsigned f = 0;
+    int rc = mht::device_status(plan->dev.ws + plan->P.status_offset(plan->dev.max_nrhs, plan->F.n, plan->F.m), stream,
+                                &f, err);
+    if (rc) return set_error(mht_status(rc), err);
+    *flags = int32_t(f);
+    if (f) return set_error(MHT_ERR_TIMEOUT, "a bounded device wait gave up (status flags " + std::to_string(f) + ")");
+    return MHT_OK;
+  });
+}
+
+mht_status mht_plan_set_path(mht_plan* plan, int32_t path) {
+  return guarded([&]() -> mht_status {
+    if (!plan || path < 0 || path > 2) mht::fail(MHT_ERR_INVALID_ARG, "bad plan or path");
+    plan->dev.path = path;
     return MHT_OK;
   });
 }
@@ -350,7 +375,7 @@ mht_status mht_plan_stage_times(mht_plan* plan, int32_t direction, double* ms, i
     if (!plan || !ms || !launches || (direction != 0 && direction != 1)) mht::fail(MHT_ERR_INVALID_ARG, "bad argument");
     if (!plan->dev.prof) mht::fail(MHT_ERR_INVALID_ARG, "stage timing is not enabled");
     std::string err;
-    int rc = mht::profiler_read(plan->dev.prof, direction, plan->F.L + 2, ms, launches, err);
+    int rc = mht::profiler_read(plan->dev.prof, direction, plan->F.L + 3, ms, launches, err);
     return rc ? set_error(mht_status(rc), err) : MHT_OK;
   });
 }

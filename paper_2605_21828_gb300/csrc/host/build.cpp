@@ -90,7 +90,7 @@ int tree_depth(int64_t n, int64_t leaf) {
 // ID of the block Phi(rows, cols); returns the block and writes the skeleton columns.
 Block factor_block(const Evaluator& ev, bool cplx, const std::vector<int64_t>& rows_all,
                    const std::vector<int64_t>& cols, double eps, double oversample,
-                   uint64_t seed, std::vector<int64_t>& skel) {
+                   uint64_t seed, std::vector<int64_t>& skel, bool blocked) {
   Block B;
   const int64_t K = int64_t(cols.size());
   B.K = int32_t(K);
@@ -119,7 +119,7 @@ Block factor_block(const Evaluator& ev, bool cplx, const std::vector<int64_t>& r
   } else {
     std::vector<double> A(size_t(M * K));
     ev.eval(rows->data(), M, cols.data(), K, A.data());
-    B.r = interpolative_decomposition_real(A.data(), M, K, eps, B.perm, B.T);
+    B.r = interpolative_decomposition_real(A.data(), M, K, eps, B.perm, B.T, seed ^ 0x5bd1e995ull, blocked);
   }
   skel.resize(B.r);
   for (int32_t i = 0; i < B.r; ++i) skel[i] = cols[B.perm[i]];
@@ -167,6 +167,7 @@ void build_factorization(const mht_problem& p, const mht_options& o, Factorizati
       if (!std::isfinite(w)) fail(MHT_ERR_NUMERIC, "non-finite weight");
   }
   std::unique_ptr<Evaluator> ev(make_evaluator(p));
+  const bool blocked = o.id_method == MHT_ID_BLOCKED || (o.id_method == MHT_ID_AUTO && p.n * p.m >= (int64_t(1) << 28));
   const int64_t nb = F.nblk();
   F.lv.assign(L + 1, std::vector<Block>(nb));
   std::vector<std::vector<int64_t>> J(nb), Jn(nb);
@@ -190,7 +191,7 @@ void build_factorization(const mht_problem& p, const mht_options& o, Factorizati
   for (int64_t nu = 0; nu < nb; ++nu)
     guarded([&] {
       std::vector<int64_t> cols(F.mode_perm.begin() + F.mode_off[nu], F.mode_perm.begin() + F.mode_off[nu + 1]);
-      F.lv[0][nu] = factor_block(*ev, F.cplx, all, cols, o.eps, o.oversample, mix(o.seed, uint64_t(nu)), J[nu]);
+      F.lv[0][nu] = factor_block(*ev, F.cplx, all, cols, o.eps, o.oversample, mix(o.seed, uint64_t(nu)), J[nu], blocked);
     });
   if (failed) throw first;
   stamp("level", 0);
@@ -207,7 +208,7 @@ void build_factorization(const mht_problem& p, const mht_options& o, Factorizati
         std::vector<int64_t> cand(J[q]);
         cand.insert(cand.end(), J[q + 1].begin(), J[q + 1].end());
         F.lv[l][b] = factor_block(*ev, F.cplx, rows, cand, o.eps, o.oversample,
-                                  mix(mix(o.seed, uint64_t(l)), uint64_t(b)), Jn[b]);
+                                  mix(mix(o.seed, uint64_t(l)), uint64_t(b)), Jn[b], blocked);
       });
     if (failed) throw first;
     J.swap(Jn);

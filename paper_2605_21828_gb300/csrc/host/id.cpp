@@ -9,6 +9,8 @@
 #include <cmath>
 #include <complex>
 #include <numeric>
+#include <random>
+#include <algorithm>
 
 #include "internal.h"
 
@@ -132,8 +134,207 @@ int qrcp_id(S* A, int64_t M, int64_t K, double eps, std::vector<int32_t>& perm,
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// Blocked column-pivoted QR with randomized block pivoting (HQRRP: Martinsson, Quintana-Orti,
+// Heavner, van de Geijn, SIAM J. Sci. Comput. 2017; Duersch & Gu 2017), real FP64.
+// A Gaussian sketch Y = G A (b + p rows) chooses b pivot columns at a time by an unblocked
+// QRCP of the small sketch; the b columns are factored by Householder QR, the trailing
+// matrix is updated with the compact WY form (GEMMs), and the sketch is downdated as
+// Y2 <- Y2 - Y1 R11^{-1} R12.  Almost all flops are matrix-matrix products.  The rank is
+// the first k with |R_kk| <= eps |R_11| (|R_11| = largest column norm, as in QRCP), or the
+// point where every remaining column norm is below that threshold.
+void gemm(bool transA, int m, int n, int k, double alpha, const double* A, int lda, const double* B, int ldb,
+          double beta, double* C, int ldc);
+
+namespace {
+
+// LAPACK-style elementary reflector: on exit x[0] = beta, x[1:] = v[1:], v[0] = 1.
+double householder(double* x, int64_t n, double* beta) {
+  if (n <= 0) { *beta = 0; return 0.0; }
+  const double alpha = x[0];
+  const double xn2 = n > 1 ? sumsq(x + 1, n - 1) : 0.0;
+  if (xn2 == 0.0) { *beta = alpha; return 0.0; }
+  const double nrm = std::sqrt(alpha * alpha + xn2);
+  const double b = alpha >= 0 ? -nrm : nrm;
+  const double tau = (b - alpha) / b;
+  const double scale = 1.0 / (alpha - b);
+  for (int64_t i = 1; i < n; ++i) x[i] *= scale;
+  x[0] = b;
+  *beta = b;
+  return tau;
+}
+
+// Unblocked QRCP on the s x k sketch Y (column-major, ld s) for `steps` pivots; records the
+// column swaps (position q <-> swaps[q]) so they can be replayed on A.
+void sketch_pivots(std::vector<double>& Y, int s, int k, int steps, std::vector<int>& swaps) {
+  std::vector<double> nr(k);
+  for (int j = 0; j < k; ++j) nr[j] = sumsq(&Y[size_t(j) * s], s);
+  swaps.assign(steps, 0);
+  for (int q = 0; q < steps; ++q) {
+    int p = q;
+    for (int j = q + 1; j < k; ++j)
+      if (nr[j] > nr[p]) p = j;
+    swaps[q] = p;
+    if (p != q) {
+      std::swap_ranges(&Y[size_t(q) * s], &Y[size_t(q + 1) * s], &Y[size_t(p) * s]);
+      std::swap(nr[q], nr[p]);
+    }
+    if (q >= s) continue;  // the sketch has no rows left to reflect
+    double* col = &Y[size_t(q) * s];
+    double beta;
+    const double tau = householder(col + q, s - q, &beta);
+    if (tau != 0.0) {
+      const double v0 = col[q];
+      col[q] = 1.0;
+      for (int j = q + 1; j < k; ++j) reflect(col + q, &Y[size_t(j) * s + q], s - q, tau);
+      col[q] = v0;
+    }
+    for (int j = q + 1; j < k; ++j) {
+      const double a = Y[size_t(j) * s + q];
+      nr[j] = std::max(0.0, nr[j] - a * a);
+    }
+  }
+}
+
+int qrcp_id_blocked(double* A, int64_t M, int64_t K, double eps, uint64_t seed, std::vector<int32_t>& perm,
+                    std::vector<double>& Tout) {
+  constexpr int b = 64, p = 8, s = b + p;
+  perm.resize(K);
+  std::iota(perm.begin(), perm.end(), 0);
+  Tout.clear();
+  double maxn = 0;
+  for (int64_t j = 0; j < K; ++j) {
+    const double v = sumsq(A + j * M, M);
+    if (!std::isfinite(v)) fail(MHT_ERR_NUMERIC, "non-finite entry in a block of Phi");
+    maxn = std::max(maxn, v);
+  }
+  if (maxn == 0.0) return 0;
+  const double thr = eps * std::sqrt(maxn);  // eps |R_11|
+  // sketch Y = G A with G Gaussian (s x M)
+  std::vector<double> G(size_t(s) * M), Y(size_t(s) * K);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> N01;
+  for (auto& g : G) g = N01(rng);
+  gemm(false, s, int(K), int(M), 1.0, G.data(), s, A, int(M), 0.0, Y.data(), s);
+  const int64_t kmax = std::min(M, K);
+  int64_t r = kmax;
+  std::vector<double> V, Tm, W, Ys, X;
+  std::vector<int> swaps;
+  for (int64_t j = 0; j < kmax; j += b) {
+    const int bb = int(std::min<int64_t>(b, kmax - j));
+    const int64_t M2 = M - j, K2 = K - j - bb;
+    // a. pivots from the sketch of the remaining columns
+    Ys.assign(Y.begin() + size_t(j) * s, Y.end());
+    sketch_pivots(Ys, s, int(K - j), bb, swaps);
+    for (int q = 0; q < bb; ++q) {
+      const int64_t a = j + q, c = j + swaps[q];
+      if (a == c) continue;
+      std::swap_ranges(A + a * M, A + (a + 1) * M, A + c * M);
+      std::swap_ranges(&Y[size_t(a) * s], &Y[size_t(a + 1) * s], &Y[size_t(c) * s]);
+      std::swap(perm[a], perm[c]);
+    }
+    // b. Householder QR of the panel A(j:M, j:j+bb); V keeps the reflectors explicitly
+    V.assign(size_t(M2) * bb, 0.0);
+    std::vector<double> tau(bb, 0.0);
+    int64_t rank_here = -1;
+    for (int q = 0; q < bb; ++q) {
+      double* col = A + (j + q) * M + j;  // rows j..M-1 of column j+q
+      double beta;
+      tau[q] = householder(col + q, M2 - q, &beta);
+      if (rank_here < 0 && !(std::fabs(beta) > thr)) rank_here = j + q;
+      double* v = &V[size_t(q) * M2];
+      v[q] = 1.0;
+      for (int64_t i = q + 1; i < M2; ++i) v[i] = col[i];
+      for (int64_t i = q + 1; i < M2; ++i) col[i] = 0.0;
+      if (tau[q] != 0.0)
+        for (int c = q + 1; c < bb; ++c) reflect(v + q, A + (j + c) * M + j + q, M2 - q, tau[q]);
+    }
+    // c. compact WY: H_0 ... H_{bb-1} = I - V T V^T (T upper triangular)
+    Tm.assign(size_t(bb) * bb, 0.0);
+    for (int q = 0; q < bb; ++q) {
+      Tm[size_t(q) * bb + q] = tau[q];
+      if (q == 0 || tau[q] == 0.0) continue;
+      std::vector<double> w(q, 0.0);  // w = -tau V(:, 0:q)^T v_q
+      const double* vq = &V[size_t(q) * M2];
+      for (int c = 0; c < q; ++c) {
+        const double* vc = &V[size_t(c) * M2];
+        double acc = 0;
+#pragma omp simd reduction(+ : acc)
+        for (int64_t i = q; i < M2; ++i) acc += vc[i] * vq[i];
+        w[c] = -tau[q] * acc;
+      }
+      for (int a = 0; a < q; ++a) {  // T(0:q, q) = T(0:q, 0:q) w
+        double acc = 0;
+        for (int c = a; c < q; ++c) acc += Tm[size_t(c) * bb + a] * w[c];
+        Tm[size_t(q) * bb + a] = acc;
+      }
+    }
+    // d. trailing update A2 <- (I - V T V^T)^T A2 = A2 - V T^T (V^T A2)
+    double* A2 = A + (j + bb) * M + j;
+    if (K2 > 0) {
+      W.assign(size_t(bb) * K2, 0.0);
+      gemm(true, bb, int(K2), int(M2), 1.0, V.data(), int(M2), A2, int(M), 0.0, W.data(), bb);
+      for (int64_t c = 0; c < K2; ++c) {  // W <- T^T W, in place from the bottom row up
+        double* wc = &W[size_t(c) * bb];
+        for (int a = bb - 1; a >= 0; --a) {
+          double acc = 0;
+          for (int q = 0; q <= a; ++q) acc += Tm[size_t(a) * bb + q] * wc[q];
+          wc[a] = acc;
+        }
+      }
+      gemm(false, int(M2), int(K2), bb, -1.0, V.data(), int(M2), W.data(), bb, 1.0, A2, int(M));
+    }
+    if (rank_here >= 0) { r = rank_here; break; }
+    // e. stop when every remaining column is below the threshold
+    double rem = 0;
+    for (int64_t c = 0; c < K2; ++c) rem = std::max(rem, sumsq(A2 + c * M + bb, M2 - bb));
+    if (K2 == 0 || std::sqrt(rem) <= thr || j + bb >= kmax) { r = std::min<int64_t>(j + bb, kmax); break; }
+    // f. sketch downdate: Y2 <- Y2 - Y1 R11^{-1} R12
+    X.assign(size_t(bb) * K2, 0.0);
+    for (int64_t c = 0; c < K2; ++c) {
+      double* xc = &X[size_t(c) * bb];
+      for (int a = bb - 1; a >= 0; --a) {
+        double acc = A2[c * M + a];
+        for (int q = a + 1; q < bb; ++q) acc -= A[(j + q) * M + j + a] * xc[q];
+        xc[a] = acc / A[(j + a) * M + j + a];
+      }
+    }
+    gemm(false, s, int(K2), bb, -1.0, &Y[size_t(j) * s], s, X.data(), bb, 1.0, &Y[size_t(j + bb) * s], s);
+  }
+  // T~ = R11^{-1} R12 by blocked back substitution (column-major work array, row-major out)
+  const int64_t nc = K - r;
+  Tout.assign(size_t(r * nc), 0.0);
+  if (r == 0 || nc == 0) return int(r);
+  std::vector<double> Tc(size_t(r) * nc);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int64_t i = 0; i < r; ++i) Tc[size_t(c) * r + i] = A[(r + c) * M + i];
+  constexpr int bs = 64;
+  for (int64_t i1 = r; i1 > 0; i1 -= bs) {
+    const int64_t i0 = std::max<int64_t>(0, i1 - bs), h = i1 - i0;
+    if (i1 < r)  // Tc(i0:i1, :) -= R(i0:i1, i1:r) Tc(i1:r, :)
+      gemm(false, int(h), int(nc), int(r - i1), -1.0, A + i1 * M + i0, int(M), &Tc[i1], int(r), 1.0, &Tc[i0], int(r));
+    for (int64_t c = 0; c < nc; ++c) {
+      double* tc = &Tc[size_t(c) * r];
+      for (int64_t a = i1 - 1; a >= i0; --a) {
+        double acc = tc[a];
+        for (int64_t q = a + 1; q < i1; ++q) acc -= A[q * M + a] * tc[q];
+        tc[a] = acc / A[a * M + a];
+      }
+    }
+  }
+  for (int64_t i = 0; i < r; ++i)
+    for (int64_t c = 0; c < nc; ++c) Tout[size_t(i) * nc + c] = Tc[size_t(c) * r + i];
+  for (double v : Tout)
+    if (!std::isfinite(v)) fail(MHT_ERR_NUMERIC, "non-finite interpolation coefficient");
+  return int(r);
+}
+
+}  // namespace
+
 int interpolative_decomposition_real(double* A, int64_t M, int64_t K, double eps,
-                                     std::vector<int32_t>& perm, std::vector<double>& T) {
+                                     std::vector<int32_t>& perm, std::vector<double>& T, uint64_t seed,
+                                     bool blocked) {
+  if (blocked && std::min(M, K) >= 128) return qrcp_id_blocked(A, M, K, eps, seed, perm, T);
   return qrcp_id<double>(A, M, K, eps, perm, T);
 }
 

@@ -68,8 +68,10 @@ void space_tree(const mht_problem& p, mht_tree_kind kind, int L, uint64_t seed,
 // Column ID of the column-major M x K matrix A (overwritten) by Householder QR with column
 // pivoting; rank = #{k : |R_kk| > eps |R_11|}.  Writes perm (skeleton first) and
 // T~ = R11^{-1} R12 (row-major r x (K-r)).  Returns r.
+// blocked = true selects the randomized block-pivoted variant (HQRRP) for large blocks.
 int interpolative_decomposition_real(double* A, int64_t M, int64_t K, double eps,
-                                     std::vector<int32_t>& perm, std::vector<double>& T);
+                                     std::vector<int32_t>& perm, std::vector<double>& T, uint64_t seed = 0,
+                                     bool blocked = false);
 int interpolative_decomposition_complex(std::complex<double>* A, int64_t M, int64_t K,
                                         double eps, std::vector<int32_t>& perm,
                                         std::vector<double>& T);
@@ -79,29 +81,54 @@ void build_factorization(const mht_problem& p, const mht_options& o, Factorizati
 void import_factors(const mht_factors& in, Factorization& F);
 
 // --- packing -------------------------------------------------------------------------------
+// Each stage is stored twice: as applied by synthesis (T~ r x K', U |tau| x r_L) and as
+// applied by the adjoint (conj(T~)^T K' x r, conj(U)^T r_L x |tau|), so both directions
+// stream contiguous rows.  dir[0] = synthesis, dir[1] = analysis.
+struct StageDir {
+  size_t desc_off = 0, items_off = 0;  // byte offsets in the image
+  int64_t nitems = 0;
+  int64_t max_ld = 0;                  // widest padded row (elements)
+  size_t max_tile_bytes = 0;           // largest work-item matrix tile
+  size_t data_bytes = 0;               // padded device bytes of this direction's matrices
+};
+
 struct Stage {
   int64_t nblocks = 0;
-  size_t desc_off = 0;          // byte offset of the MhtBlockDesc array
-  size_t items_syn_off = 0, items_adj_off = 0;
-  int64_t nitems_syn = 0, nitems_adj = 0;
-  int64_t out_entries = 0;      // entries of this stage's output vector (per RHS)
-  int64_t in_entries = 0;       // entries of its input vector (per RHS)
-  int64_t max_k = 0;            // largest K (ID) or |tau| (U)
-  int64_t max_rows = 0, max_cols = 0;
-  int64_t t_entries = 0;        // stored matrix entries
-  size_t data_bytes = 0;        // padded device bytes of the matrices
+  int64_t out_entries = 0;      // entries of the synthesis output vector (per RHS)
+  int64_t in_entries = 0;       // entries of the synthesis input vector (per RHS)
+  int64_t max_rank = 0;
+  int64_t t_entries = 0;        // stored matrix entries (one orientation)
   size_t alg_bytes = 0;         // algorithmic bytes of one single-RHS launch
-  int rows_per_item = 0, cols_per_item = 0;
+  StageDir dir[2];
+};
+
+// Persistent (fused) apply of one direction: all stages in one launch, dependency order.
+struct FusedDir {
+  size_t desc_all_off = 0;      // [(L+2) * nb] descriptors, stage-major (= dir desc arrays)
+  size_t targets_off = 0;       // [(L+2) * nb] int32 persistent items per block
+  size_t items_off = 0;         // persistent work list
+  int64_t nitems = 0;
+  size_t slot_bytes = 0;        // bytes of one ring slot (>= the widest row)
+  int64_t max_ld = 0;
+  int64_t max_item_rows = 0;    // largest persistent item (rows)
 };
 
 struct Packed {
   bool fp64 = false, cplx = false;
   int elem_bytes = 4;           // bytes of one (possibly complex) element
+  int L = 0;
+  int64_t nb = 0;
   std::vector<uint8_t> image;
-  size_t data_off = 0, index_off = 0, perm_off = 0, weights_off = 0;
+  size_t data_off = 0, index_off = 0, perm_off = 0, weights_off = 0, vecoff_off = 0;
   std::vector<Stage> st;        // L+2 stages: ID levels 0..L, then U
-  int64_t vec_entries = 0;      // max butterfly-vector length (per RHS)
+  FusedDir fused[2];
+  std::vector<int64_t> vec_off; // [L+2] offsets of the level vectors (per RHS), vec_off[L+1] = total
+  int64_t vec_entries = 0;      // total butterfly-vector entries over all levels (per RHS)
   int64_t index_entries = 0;
+  // workspace: Y, A0, A1 level vectors, host staging for c and f, counters, status word
+  size_t ws_vec_bytes(int64_t nrhs) const;
+  size_t ws_counters_offset(int64_t nrhs, int64_t n, int64_t m) const;
+  size_t status_offset(int64_t nrhs, int64_t n, int64_t m) const;
   size_t workspace_bytes(int64_t nrhs, int64_t n, int64_t m) const;
 };
 void pack(const Factorization& F, bool fp64, Packed& P);
@@ -117,6 +144,7 @@ struct DeviceView {
   size_t ws_bytes = 0;
   int64_t max_nrhs = 0;
   Profiler* prof = nullptr;       // non-null while stage timing is enabled
+  int path = 0;                   // 0 auto, 1 per-stage launches, 2 fused persistent launch
 };
 Profiler* profiler_create();
 void profiler_destroy(Profiler* p);
@@ -127,11 +155,13 @@ int apply_synthesize(const Factorization& F, const Packed& P, const DeviceView& 
 int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, const void* f,
                   int64_t ldf, void* c, int64_t ldc, int64_t nrhs, bool weighted,
                   mht_apply_mode mode, void* stream, std::string& err);
-int64_t apply_launches(const Packed& P, int64_t nrhs, mht_apply_mode mode);
+int64_t apply_launches(const Packed& P, int64_t nrhs, mht_apply_mode mode, int path);
 int device_upload(void* dst, const void* src, size_t bytes, void* stream, std::string& err);
 int device_copy_async(void* dst, const void* src, size_t bytes, int kind, void* stream,
                       std::string& err);
 int device_sync(void* stream, std::string& err);
+// Copies the device status word to *flags, clears it, and synchronizes the stream.
+int device_status(void* status_dev, void* stream, unsigned* flags, std::string& err);
 }  // namespace mht
 
 struct mht_plan {

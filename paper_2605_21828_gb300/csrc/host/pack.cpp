@@ -1,11 +1,13 @@
 // Packing of a factorization into the device image (layout in ../layout.h).
 //
-// Every stored matrix is laid out row-major with rows padded to 16 bytes so that kernels
-// stream it with aligned 128-bit loads; matrices follow each other in apply order, so one
-// stage's data is one contiguous span.  Index lists are made absolute (level 0 composes the
-// frequency-tree permutation, levels >= 1 add the offset of the input pair), so kernels
-// gather without further indirection.  Work items split large blocks into row tiles
-// (synthesis) and column tiles (analysis) of roughly equal byte counts.
+// Every stored matrix is laid out row-major with rows padded to 16 bytes, in two
+// orientations: as synthesis applies it (T~ is r x K', U_tau is |tau| x r_L) and as the
+// adjoint applies it (conj(T~)^T is K' x r, conj(U_tau)^T is r_L x |tau|).  With both
+// orientations each direction is a set of independent row-times-vector products over
+// contiguous rows, split into work items (block, row range) of about kTileBytes so a CTA
+// stages one item's rows into shared memory with a single bulk copy.  Index lists are
+// absolute (level 0 composes the frequency-tree permutation, levels >= 1 add the offset of
+// the input pair), so kernels gather without further indirection.
 #include <algorithm>
 #include <cstring>
 
@@ -16,16 +18,31 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-constexpr size_t kItemBytes = 48 * 1024;   // target matrix bytes per synthesis work item
-constexpr int kWarps = 8;                  // warps per CTA of the SIMT apply kernels
+constexpr size_t kTileBytes = 32 * 1024;    // target matrix bytes per per-stage work item
+constexpr size_t kPItemBytes = 256 * 1024;  // largest persistent work item
+constexpr int kPItemRows = 1024;             // and at most this many rows (staged per item)
+constexpr size_t kSlotBytes = 32 * 1024;    // ring slot of the persistent kernel
 
 }  // namespace
 
-size_t Packed::workspace_bytes(int64_t nrhs, int64_t n, int64_t m) const {
-  const size_t vec = align_up(size_t(std::max<int64_t>(vec_entries, 1)) * nrhs * elem_bytes, 256);
+size_t Packed::ws_vec_bytes(int64_t nrhs) const {
+  return align_up(size_t(std::max<int64_t>(vec_entries, 1)) * nrhs * elem_bytes, 256);
+}
+
+size_t Packed::ws_counters_offset(int64_t nrhs, int64_t n, int64_t m) const {
   const size_t sc = align_up(size_t(m) * nrhs * elem_bytes, 256);
   const size_t sf = align_up(size_t(n) * nrhs * elem_bytes, 256);
-  return 4 * vec + sc + sf + 256;
+  return 3 * ws_vec_bytes(nrhs) + sc + sf;
+}
+
+size_t Packed::status_offset(int64_t nrhs, int64_t n, int64_t m) const {
+  // counters: per direction (L+2) * nb completion counts, then two queue heads
+  const size_t cnt = align_up((size_t(2) * (L + 2) * nb + 2) * sizeof(unsigned), 256);
+  return ws_counters_offset(nrhs, n, m) + cnt;
+}
+
+size_t Packed::workspace_bytes(int64_t nrhs, int64_t n, int64_t m) const {
+  return status_offset(nrhs, n, m) + 256;
 }
 
 void pack(const Factorization& F, bool fp64, Packed& P) {
@@ -34,141 +51,178 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
   P.cplx = F.cplx;
   const int W = F.cplx ? 2 : 1;
   const int sb = fp64 ? 8 : 4;             // bytes of one real scalar
-  P.elem_bytes = sb * W;
-  const int E = 16 / P.elem_bytes;          // elements per 16-byte vector
+  const int es = sb * W;
+  P.elem_bytes = es;
+  const int E = 16 / es;                    // elements per 16-byte vector
   const int L = F.L;
   const int64_t nb = F.nblk();
+  P.L = L;
+  P.nb = nb;
   const int nst = L + 2;
   P.st.assign(nst, Stage());
+  auto pad = [&](int64_t c) { return (c + E - 1) / E * E; };
 
-  // vector offsets per level
+  // butterfly-vector offsets per level
   std::vector<std::vector<int64_t>> off(L + 1, std::vector<int64_t>(nb + 1, 0));
   for (int l = 0; l <= L; ++l)
     for (int64_t b = 0; b < nb; ++b) off[l][b + 1] = off[l][b] + F.lv[l][b].r;
-  P.vec_entries = 0;
-  for (int l = 0; l <= L; ++l) P.vec_entries = std::max(P.vec_entries, off[l][nb]);
+  P.vec_off.assign(L + 2, 0);
+  for (int l = 0; l <= L; ++l) P.vec_off[l + 1] = P.vec_off[l] + off[l][nb];
+  P.vec_entries = P.vec_off[L + 1];
 
-  // data section sizes
-  std::vector<std::vector<MhtBlockDesc>> desc(nst, std::vector<MhtBlockDesc>(nb));
-  int64_t elem = 0;    // running element offset in [data]
-  int64_t ient = 0;    // running offset in [index]
-  for (int l = 0; l <= L; ++l) {
-    Stage& S = P.st[l];
-    S.nblocks = nb;
-    S.in_entries = (l == 0) ? F.m : off[l - 1][nb];
-    S.out_entries = off[l][nb];
-    for (int64_t b = 0; b < nb; ++b) {
-      const Block& B = F.lv[l][b];
-      const int cols = B.K - B.r;
-      const int ldt = int((cols + E - 1) / E * E);
-      MhtBlockDesc& d = desc[l][b];
-      d.t_off = elem;
-      d.ldt = ldt;
-      d.rows = B.r;
-      d.cols = cols;
-      d.idx_off = int(ient);
-      d.out_off = int(off[l][b]);
-      d.in_off = (l == 0) ? int(F.mode_off[b]) : int(off[l - 1][F.pair_index(l, b)]);
-      elem += int64_t(B.r) * ldt;
-      ient += B.K;
-      S.t_entries += int64_t(B.r) * cols;
-      S.max_k = std::max<int64_t>(S.max_k, B.K);
-      S.max_rows = std::max<int64_t>(S.max_rows, B.r);
-      S.max_cols = std::max<int64_t>(S.max_cols, cols);
-    }
-    S.data_bytes = size_t(elem - desc[l][0].t_off) * P.elem_bytes;
-  }
-  {
-    Stage& S = P.st[L + 1];
-    S.nblocks = nb;
-    S.in_entries = off[L][nb];
-    S.out_entries = F.n;
-    const int64_t start = elem;
-    for (int64_t t = 0; t < nb; ++t) {
-      const int rows = int(F.leaf_rows(t));
-      const int cols = F.lv[L][t].r;
-      const int ldt = int((cols + E - 1) / E * E);
-      MhtBlockDesc& d = desc[L + 1][t];
-      d.t_off = elem;
-      d.ldt = ldt;
-      d.rows = rows;
-      d.cols = cols;
-      d.idx_off = -1;
-      d.out_off = int(F.space_off[t]);
-      d.in_off = int(off[L][t]);
-      elem += int64_t(rows) * ldt;
-      S.t_entries += int64_t(rows) * cols;
-      S.max_k = std::max<int64_t>(S.max_k, rows);
-      S.max_rows = std::max<int64_t>(S.max_rows, rows);
-      S.max_cols = std::max<int64_t>(S.max_cols, cols);
-    }
-    S.data_bytes = size_t(elem - start) * P.elem_bytes;
-  }
-  P.index_entries = ient;
-  // algorithmic bytes per single-RHS launch: matrices (unpadded), indices, descriptors,
-  // gathered inputs and written outputs
-  for (int l = 0; l <= L; ++l) {
-    Stage& S = P.st[l];
-    int64_t sumk = 0, sumr = 0;
-    for (int64_t b = 0; b < nb; ++b) { sumk += F.lv[l][b].K; sumr += F.lv[l][b].r; }
-    S.alg_bytes = size_t(S.t_entries) * P.elem_bytes + size_t(sumk) * 4 + size_t(nb) * sizeof(MhtBlockDesc) +
-                  size_t(sumk + sumr) * P.elem_bytes;
-  }
-  {
-    Stage& S = P.st[L + 1];
-    int64_t sumr = 0;
-    for (int64_t t = 0; t < nb; ++t) sumr += F.lv[L][t].r;
-    S.alg_bytes = size_t(S.t_entries) * P.elem_bytes + size_t(nb) * sizeof(MhtBlockDesc) +
-                  size_t(sumr) * P.elem_bytes + size_t(F.n) * (4 + P.elem_bytes);
-  }
-
-  // work items
-  std::vector<std::vector<MhtItem>> isyn(nst), iadj(nst);
-  const int cols_per_item = 32 * E * 2;  // two 16-byte vectors per lane
+  // descriptors for both directions; matrix element offsets run synthesis data first
+  // (stages 0..L+1), then adjoint data (stages L+1..0)
+  std::vector<std::vector<MhtBlockDesc>> desc[2];
+  desc[0].assign(nst, std::vector<MhtBlockDesc>(nb));
+  desc[1].assign(nst, std::vector<MhtBlockDesc>(nb));
+  int64_t elem = 0, ient = 0;
   for (int s = 0; s < nst; ++s) {
     Stage& S = P.st[s];
-    S.cols_per_item = cols_per_item;
-    int64_t maxldt = 0;
-    for (int64_t b = 0; b < nb; ++b) maxldt = std::max<int64_t>(maxldt, desc[s][b].ldt);
+    S.nblocks = nb;
+    const int64_t start = elem;
     for (int64_t b = 0; b < nb; ++b) {
-      const MhtBlockDesc& d = desc[s][b];
-      const int64_t rowbytes = int64_t(std::max(d.ldt, E)) * P.elem_bytes;
-      int rpi = int(std::max<int64_t>(kWarps, int64_t(kItemBytes) / rowbytes));
-      rpi = (rpi + kWarps - 1) / kWarps * kWarps;
-      for (int r0 = 0; r0 < d.rows; r0 += rpi)
-        isyn[s].push_back({int(b), r0, std::min(rpi, d.rows - r0), 0});
-      const bool id_stage = (s <= L);
-      const int sib = (id_stage && s >= 1) ? int((b >> (L - s)) & 1) : 0;
-      const int ncol_total = d.cols;
-      const bool has_out = id_stage ? (d.rows + d.cols > 0) : (d.cols > 0);
-      if (!has_out) continue;
-      if (ncol_total == 0) {
-        iadj[s].push_back({int(b), 0, 0, sib});
+      MhtBlockDesc& d = desc[0][s][b];
+      if (s <= L) {
+        const Block& B = F.lv[s][b];
+        d.rows = B.r;
+        d.cols = B.K - B.r;
+        d.idx_off = int(ient);
+        d.out_off = int(off[s][b]);
+        d.in_off = (s == 0) ? int(F.mode_off[b]) : int(off[s - 1][F.pair_index(s, b)]);
+        ient += B.K;
+        S.max_rank = std::max<int64_t>(S.max_rank, B.r);
       } else {
-        for (int c0 = 0; c0 < ncol_total; c0 += cols_per_item)
-          iadj[s].push_back({int(b), c0, std::min(cols_per_item, ncol_total - c0), sib});
+        d.rows = int(F.leaf_rows(b));
+        d.cols = F.lv[L][b].r;
+        d.idx_off = -1;
+        d.out_off = int(F.space_off[b]);
+        d.in_off = int(off[L][b]);
+        S.max_rank = std::max<int64_t>(S.max_rank, d.cols);
+      }
+      d.ldt = int(pad(d.cols));
+      d.t_off = elem;
+      elem += int64_t(d.rows) * d.ldt;
+      S.t_entries += int64_t(d.rows) * d.cols;
+      S.dir[0].max_ld = std::max<int64_t>(S.dir[0].max_ld, d.ldt);
+    }
+    S.dir[0].data_bytes = size_t(elem - start) * es;
+    S.in_entries = (s == 0) ? F.m : off[s - 1][nb];
+    S.out_entries = (s <= L) ? off[s][nb] : F.n;
+  }
+  for (int s = nst - 1; s >= 0; --s) {
+    Stage& S = P.st[s];
+    const int64_t start = elem;
+    for (int64_t b = 0; b < nb; ++b) {
+      const MhtBlockDesc& d0 = desc[0][s][b];
+      MhtBlockDesc& d = desc[1][s][b];
+      d = d0;
+      d.rows = d0.cols;  // transposed
+      d.cols = d0.rows;
+      d.ldt = int(pad(d.cols));
+      d.t_off = elem;
+      elem += int64_t(d.rows) * d.ldt;
+      S.dir[1].max_ld = std::max<int64_t>(S.dir[1].max_ld, d.ldt);
+    }
+    S.dir[1].data_bytes = size_t(elem - start) * es;
+  }
+  P.index_entries = ient;
+
+  // algorithmic bytes per single-RHS launch: matrices (unpadded), indices, descriptors,
+  // gathered inputs and written outputs (the same for both directions)
+  for (int s = 0; s < nst; ++s) {
+    Stage& S = P.st[s];
+    if (s <= L) {
+      int64_t sumk = 0, sumr = 0;
+      for (int64_t b = 0; b < nb; ++b) { sumk += F.lv[s][b].K; sumr += F.lv[s][b].r; }
+      S.alg_bytes = size_t(S.t_entries) * es + size_t(sumk) * 4 + size_t(nb) * sizeof(MhtBlockDesc) +
+                    size_t(sumk + sumr) * es;
+    } else {
+      int64_t sumr = 0;
+      for (int64_t t = 0; t < nb; ++t) sumr += F.lv[L][t].r;
+      S.alg_bytes = size_t(S.t_entries) * es + size_t(nb) * sizeof(MhtBlockDesc) + size_t(sumr) * es +
+                    size_t(F.n) * (4 + es);
+    }
+  }
+
+  // work items: row ranges of about kTileBytes
+  std::vector<std::vector<MhtItem>> items[2];
+  items[0].assign(nst, {});
+  items[1].assign(nst, {});
+  for (int dir = 0; dir < 2; ++dir)
+    for (int s = 0; s < nst; ++s) {
+      StageDir& D = P.st[s].dir[dir];
+      for (int64_t b = 0; b < nb; ++b) {
+        const MhtBlockDesc& d = desc[dir][s][b];
+        const int sib = (dir == 1 && s >= 1 && s <= L) ? int((b >> (L - s)) & 1) : 0;
+        const size_t rowbytes = size_t(d.ldt) * es;
+        const int rpi = int(std::max<size_t>(1, rowbytes ? kTileBytes / rowbytes : size_t(1) << 20));
+        if (d.rows == 0) {
+          // adjoint of an ID block without T~ (full rank): still copies the skeleton out
+          if (dir == 1 && s <= L && d.cols > 0) items[dir][s].push_back({int(b), 0, 0, sib});
+          continue;
+        }
+        for (int r0 = 0; r0 < d.rows; r0 += rpi) {
+          const int cnt = std::min(rpi, d.rows - r0);
+          items[dir][s].push_back({int(b), r0, cnt, sib});
+          D.max_tile_bytes = std::max(D.max_tile_bytes, size_t(cnt) * rowbytes);
+        }
+      }
+      D.nitems = int64_t(items[dir][s].size());
+    }
+
+  // persistent work lists: dependency order (synthesis 0..L+1, analysis L+1..0), items of
+  // at most kPItemBytes, and the number of items per (stage, block) as completion targets
+  std::vector<MhtPItem> pitems[2];
+  std::vector<int32_t> targets[2];
+  for (int dir = 0; dir < 2; ++dir) {
+    targets[dir].assign(size_t(nst) * nb, 0);
+    FusedDir& FD = P.fused[dir];
+    FD.slot_bytes = kSlotBytes;
+    for (int k = 0; k < nst; ++k) {
+      const int s = dir == 0 ? k : nst - 1 - k;
+      for (int64_t b = 0; b < nb; ++b) {
+        const MhtBlockDesc& d = desc[dir][s][b];
+        const size_t rowbytes = size_t(d.ldt) * es;
+        FD.slot_bytes = std::max(FD.slot_bytes, (rowbytes + 127) / 128 * 128);
+        FD.max_ld = std::max<int64_t>(FD.max_ld, d.ldt);
+        int n_it = 0;
+        if (d.rows == 0) {
+          if (dir == 1 && s <= L && d.cols > 0) {
+            pitems[dir].push_back({s, int(b), 0, 0});
+            n_it = 1;
+          }
+        } else {
+          const int rpi = int(std::min<size_t>(kPItemRows, std::max<size_t>(1, rowbytes ? kPItemBytes / rowbytes
+                                                                                         : size_t(kPItemRows))));
+          for (int r0 = 0; r0 < d.rows; r0 += rpi, ++n_it) pitems[dir].push_back({s, int(b), r0, std::min(rpi, d.rows - r0)});
+        }
+        targets[dir][size_t(s) * nb + b] = n_it;
       }
     }
-    S.rows_per_item = 0;
-    S.nitems_syn = int64_t(isyn[s].size());
-    S.nitems_adj = int64_t(iadj[s].size());
-    (void)maxldt;
+    FD.nitems = int64_t(pitems[dir].size());
+    for (const MhtPItem& it : pitems[dir]) FD.max_item_rows = std::max<int64_t>(FD.max_item_rows, it.count);
   }
 
   // assemble the image
-  size_t pos = 0;
+  size_t pos = align_up(size_t(elem) * es, 256);
   P.data_off = 0;
-  pos = align_up(size_t(elem) * P.elem_bytes, 256);
   P.index_off = pos;
   pos = align_up(pos + size_t(ient) * 4, 256);
-  for (int s = 0; s < nst; ++s) {
-    P.st[s].desc_off = pos;
-    pos = align_up(pos + size_t(nb) * sizeof(MhtBlockDesc), 256);
-    P.st[s].items_syn_off = pos;
-    pos = align_up(pos + isyn[s].size() * sizeof(MhtItem), 256);
-    P.st[s].items_adj_off = pos;
-    pos = align_up(pos + iadj[s].size() * sizeof(MhtItem), 256);
+  for (int dir = 0; dir < 2; ++dir) {
+    P.fused[dir].desc_all_off = pos;  // stage-major, contiguous over the stages
+    for (int s = 0; s < nst; ++s) P.st[s].dir[dir].desc_off = pos + size_t(s) * nb * sizeof(MhtBlockDesc);
+    pos = align_up(pos + size_t(nst) * nb * sizeof(MhtBlockDesc), 256);
+    for (int s = 0; s < nst; ++s) {
+      P.st[s].dir[dir].items_off = pos;
+      pos = align_up(pos + items[dir][s].size() * sizeof(MhtItem), 256);
+    }
+    P.fused[dir].targets_off = pos;
+    pos = align_up(pos + targets[dir].size() * 4, 256);
+    P.fused[dir].items_off = pos;
+    pos = align_up(pos + pitems[dir].size() * sizeof(MhtPItem), 256);
   }
+  P.vecoff_off = pos;
+  pos = align_up(pos + P.vec_off.size() * 8, 256);
   P.perm_off = pos;
   pos = align_up(pos + size_t(F.n) * 4, 256);
   P.weights_off = pos;
@@ -176,36 +230,46 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
   P.image.assign(pos, 0);
   uint8_t* img = P.image.data();
 
-  auto put = [&](int64_t eoff, const double* src, int64_t rows, int64_t cols, int ldt) {
-    for (int64_t i = 0; i < rows; ++i)
-      for (int64_t j = 0; j < cols; ++j)
-        for (int c = 0; c < W; ++c) {
-          const double v = src[(i * cols + j) * W + c];
-          const size_t at = size_t((eoff + i * ldt + j) * W + c);
-          if (fp64) reinterpret_cast<double*>(img)[at] = v;
-          else reinterpret_cast<float*>(img)[at] = float(v);
-        }
+  // element (i, j) of a row-major matrix with W scalars per element; conj negates imag
+  auto store = [&](int64_t eoff, int64_t i, int64_t j, int ldt, const double* v, bool conj) {
+    for (int c = 0; c < W; ++c) {
+      const double x = (conj && c == 1) ? -v[c] : v[c];
+      const size_t at = size_t((eoff + i * ldt + j) * W + c);
+      if (fp64) reinterpret_cast<double*>(img)[at] = x;
+      else reinterpret_cast<float*>(img)[at] = float(x);
+    }
   };
   int32_t* idx = reinterpret_cast<int32_t*>(img + P.index_off);
-  for (int l = 0; l <= L; ++l)
+  for (int s = 0; s < nst; ++s)
     for (int64_t b = 0; b < nb; ++b) {
-      const Block& B = F.lv[l][b];
-      const MhtBlockDesc& d = desc[l][b];
-      put(d.t_off, B.T.data(), B.r, B.K - B.r, d.ldt);
-      for (int j = 0; j < B.K; ++j) {
-        const int64_t loc = B.perm[j];
-        idx[d.idx_off + j] = int32_t(l == 0 ? F.mode_perm[F.mode_off[b] + loc] : int64_t(d.in_off) + loc);
+      const MhtBlockDesc& d = desc[0][s][b];
+      const MhtBlockDesc& dt = desc[1][s][b];
+      const double* src = (s <= L) ? F.lv[s][b].T.data() : F.U[b].data();
+      for (int64_t i = 0; i < d.rows; ++i)
+        for (int64_t j = 0; j < d.cols; ++j) {
+          const double* v = src + (i * d.cols + j) * W;
+          store(d.t_off, i, j, d.ldt, v, false);
+          store(dt.t_off, j, i, dt.ldt, v, true);
+        }
+      if (s <= L) {
+        const Block& B = F.lv[s][b];
+        for (int j = 0; j < B.K; ++j) {
+          const int64_t loc = B.perm[j];
+          idx[d.idx_off + j] = int32_t(s == 0 ? F.mode_perm[F.mode_off[b] + loc] : int64_t(d.in_off) + loc);
+        }
       }
     }
-  for (int64_t t = 0; t < nb; ++t) {
-    const MhtBlockDesc& d = desc[L + 1][t];
-    put(d.t_off, F.U[t].data(), d.rows, d.cols, d.ldt);
+  for (int dir = 0; dir < 2; ++dir) {
+    for (int s = 0; s < nst; ++s) {
+      std::memcpy(img + P.st[s].dir[dir].desc_off, desc[dir][s].data(), size_t(nb) * sizeof(MhtBlockDesc));
+      if (!items[dir][s].empty())
+        std::memcpy(img + P.st[s].dir[dir].items_off, items[dir][s].data(), items[dir][s].size() * sizeof(MhtItem));
+    }
+    std::memcpy(img + P.fused[dir].targets_off, targets[dir].data(), targets[dir].size() * 4);
+    if (!pitems[dir].empty())
+      std::memcpy(img + P.fused[dir].items_off, pitems[dir].data(), pitems[dir].size() * sizeof(MhtPItem));
   }
-  for (int s = 0; s < nst; ++s) {
-    std::memcpy(img + P.st[s].desc_off, desc[s].data(), size_t(nb) * sizeof(MhtBlockDesc));
-    if (!isyn[s].empty()) std::memcpy(img + P.st[s].items_syn_off, isyn[s].data(), isyn[s].size() * sizeof(MhtItem));
-    if (!iadj[s].empty()) std::memcpy(img + P.st[s].items_adj_off, iadj[s].data(), iadj[s].size() * sizeof(MhtItem));
-  }
+  std::memcpy(img + P.vecoff_off, P.vec_off.data(), P.vec_off.size() * 8);
   int32_t* perm = reinterpret_cast<int32_t*>(img + P.perm_off);
   for (int64_t i = 0; i < F.n; ++i) perm[i] = int32_t(F.space_perm[i]);
   for (int64_t i = 0; i < F.n; ++i) {

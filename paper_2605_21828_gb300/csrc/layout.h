@@ -33,5 +33,13 @@ struct MhtItem {        // 16 bytes
   int sib;              // analysis of ID levels >= 1: sibling buffer (tau & 1)
 };
 
+struct MhtPItem {       // persistent work item: rows [start, start+count) of one block
+  int stage;            // 0..L transfer levels, L+1 column bases
+  int blk;
+  int start;
+  int count;
+};
+
 static_assert(sizeof(MhtBlockDesc) == 32, "descriptor size");
+static_assert(sizeof(MhtPItem) == 16, "persistent item size");
 static_assert(sizeof(MhtItem) == 16, "item size");

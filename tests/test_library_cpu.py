@@ -218,3 +218,21 @@ def test_fem_dense_build_and_analysis_inverts_synthesis(mht_lib):
     # Phi^T M Phi = I, so analysis (weights = lumped mass) undoes synthesis
     c2 = B.analyze(F, f, Md)
     assert np.linalg.norm(c2 - c) / np.linalg.norm(c) < 1e-6
+
+
+def test_blocked_randomized_pivoting_id_matches_dense(mht_lib):
+    # the block-pivoted ID (HQRRP) must keep the paper's accuracy: error about eps
+    n, eps = 4096, 1e-6
+    X, Phi, lam = _sphere(n, 63)
+    errs = {}
+    for meth in ("blocked", "classical"):
+        p = _plan_cls().build(n=n, m=Phi.shape[1], eigenvalues=lam, evaluator="sphere", points=X, eps=eps,
+                              leaf_size=128, id_method=meth)
+        F = arrays_to_oracle(p.export())
+        c = W.sphere_coefficients(Phi.shape[1])[:, 0]
+        ref = Phi @ c
+        errs[meth] = np.linalg.norm(B.synthesize(F, c) - ref) / np.linalg.norm(ref)
+        g = W.gaussian(n, 3)
+        refa = Phi.T @ g
+        assert np.linalg.norm(B.analyze(F, g) - refa) / np.linalg.norm(refa) < 10 * eps
+    assert errs["blocked"] < 10 * eps and errs["classical"] < 10 * eps
