@@ -253,6 +253,25 @@ mht_status mht_analyze_host(mht_plan* plan, const void* f_host, int64_t ldf, voi
 /* Number of kernel launches one mht_synthesize / mht_analyze call makes for nrhs. */
 mht_status mht_apply_launch_count(const mht_plan* plan, int64_t nrhs, int64_t* launches);
 
+/* Synthesis f = Phi c of one vector for callers that cannot allocate device memory: code
+ * that runs where cudaMalloc is not allowed (for instance inside a framework that owns the
+ * device memory, or a region that must not allocate).  The paper has no counterpart; this
+ * is a deployment variant of the persistent synthesis for real FP32 plans.  Its scratch
+ * (the per-level butterfly vectors, per-block completion counters, the work-queue head and a
+ * status word) lives in a fixed array of MHT_NOALLOC_SCRATCH_BYTES inside this library, which
+ * every GPU that loads the library reserves until the process exits; a plan that needs more
+ * is rejected with MHT_ERR_UNSUPPORTED and a message that gives both sizes.  Nothing is
+ * allocated: the caller passes factor_dev (the plan's packed factors on the device,
+ * 256-byte aligned -- for instance the buffer given to mht_plan_bind_device), c_dev (m floats)
+ * and f_dev (n floats).  The first call on a device looks up the array's address on that
+ * device; make that call before any stream capture.  All calls share the one array, which
+ * keeps the previous call's contents (the call clears the parts that must start at zero):
+ * calls that overlap on the GPU -- on different streams or from different threads -- race and
+ * give wrong results, so serialize them.  Asynchronous on `stream`. */
+#define MHT_NOALLOC_SCRATCH_BYTES (16u << 20)
+mht_status mht_synthesize_noalloc(const mht_plan* plan, const void* factor_dev, const void* c_dev,
+                                  void* f_dev, void* stream);
+
 /* Reads and clears the device status word of the bound workspace (synchronizes `stream`).
  * Kernels set bit 0 when a bounded wait for a bulk copy gives up instead of spinning
  * forever; the affected outputs are then unspecified.  Returns MHT_OK with *flags = 0 when

@@ -82,6 +82,7 @@ SIGNATURES = {
                                    C.c_void_p]),
     "mht_apply_launch_count": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "mht_plan_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "mht_synthesize_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mht_plan_set_path": (C.c_int, [C.c_void_p, C.c_int32]),
     "mht_plan_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "mht_plan_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

@@ -1062,3 +1062,112 @@ int device_status(void* status_dev, void* stream, unsigned* flags, std::string& 
 }
 
 }  // namespace mht
+
+// ---------------------------------------------------------------------------------------
+// Synthesis for callers that cannot allocate device memory (mht_synthesize_noalloc).
+//
+// The fused synthesis kernel needs scratch beyond its inputs and outputs: the per-level
+// butterfly vectors, one completion counter per block, the work-queue head and the status
+// word.  Here that scratch is a fixed array in this library's device image, so the caller
+// only passes the packed factors, c and f.  The array is reserved on every GPU that loads
+// the library until the process exits.  Host code must not pass the array's name to a
+// kernel (in host code it is a host-side stand-in); its device address is looked up once per
+// device with cudaGetSymbolAddress while that device is current.
+#include <mutex>
+
+namespace mht {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // MHT_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[256] = {};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void* c, void* f, void* stream,
+                             std::string& err) {
+  if (P.fp64 || P.cplx) {
+    err = "the no-alloc synthesis serves real FP32 plans";
+    return MHT_ERR_UNSUPPORTED;
+  }
+  const size_t ncnt = size_t(P.L + 2) * P.nb + 1;
+  const size_t y_bytes = align256(size_t(std::max<int64_t>(P.vec_entries, 1)) * sizeof(float));
+  const size_t cnt_bytes = align256(ncnt * sizeof(unsigned));
+  const size_t need = y_bytes + cnt_bytes + 256;
+  if (need > kNoAllocScratchBytes) {
+    err = "this plan needs " + std::to_string(need) + " bytes of scratch; the no-alloc entry point has " +
+          std::to_string(kNoAllocScratchBytes);
+    return MHT_ERR_UNSUPPORTED;
+  }
+  const size_t smem = fused_smem(P, 0, 1);
+  if (smem > 227 * 1024) {
+    err = "the fused synthesis does not fit in shared memory for this plan";
+    return MHT_ERR_UNSUPPORTED;
+  }
+  int dev = 0;
+  if (int rc = check(cudaGetDevice(&dev), err, "cudaGetDevice")) return rc;
+  if (dev < 0 || dev >= 256) {
+    err = "device ordinal out of range";
+    return MHT_ERR_INVALID_ARG;
+  }
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {  // set-up: once per device, with that device current
+      void* a = nullptr;
+      if (int rc = check(cudaGetSymbolAddress(&a, g_noalloc_scratch), err, "cudaGetSymbolAddress")) return rc;
+      g_noalloc_addr[dev] = a;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  auto* scratch = static_cast<uint8_t*>(base);
+  unsigned* cnt = reinterpret_cast<unsigned*>(scratch + y_bytes);
+  unsigned* status = reinterpret_cast<unsigned*>(scratch + y_bytes + cnt_bytes);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: counters, queue head and status start at zero
+  if (int rc = check(cudaMemsetAsync(cnt, 0, cnt_bytes + 256, s), err, "scratch reset")) return rc;
+  const FusedDir& FD = P.fused[0];
+  if (FD.nitems == 0) return 0;
+  auto kern = k_fused<float, false, 1, 0>;
+  if (int rc = check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), err,
+                     "shared memory attribute"))
+    return rc;
+  const uint8_t* img = static_cast<const uint8_t*>(factor_dev);
+  FusedParams<float> p{};
+  p.data = reinterpret_cast<const float*>(img + P.data_off);
+  p.idx = reinterpret_cast<const int*>(img + P.index_off);
+  p.perm = reinterpret_cast<const int*>(img + P.perm_off);
+  p.wts = nullptr;
+  p.desc = reinterpret_cast<const MhtBlockDesc*>(img + FD.desc_all_off);
+  p.targets = reinterpret_cast<const int*>(img + FD.targets_off);
+  p.items = reinterpret_cast<const MhtPItem*>(img + FD.items_off);
+  p.nitems = int(FD.nitems);
+  p.vec_off = reinterpret_cast<const long long*>(img + P.vecoff_off);
+  p.cin = static_cast<const float*>(c);
+  p.cout = nullptr;
+  p.fin = nullptr;
+  p.fout = static_cast<float*>(f);
+  p.ldc = 1;  // single right-hand side: leading dimensions are irrelevant
+  p.ldf = 1;
+  p.Y = reinterpret_cast<float*>(scratch);
+  p.A0 = nullptr;
+  p.A1 = nullptr;
+  p.done = cnt;
+  p.queue = cnt + ncnt - 1;
+  p.status = status;
+  p.L = P.L;
+  p.nb = int(P.nb);
+  p.nrhs = 1;
+  p.slot_bytes = int(FD.slot_bytes);
+  p.ldx = int(std::max<int64_t>(FD.max_ld, 1));
+  p.mrows = int(std::max<int64_t>(FD.max_item_rows, 1));
+  const int grid = int(std::min<int64_t>(num_sms(), FD.nitems));
+  kern<<<grid, kFusedThreads, smem, s>>>(p);
+  return check(cudaGetLastError(), err, "no-alloc synthesis launch");
+}
+
+}  // namespace mht

@@ -335,6 +335,17 @@ mht_status mht_apply_launch_count(const mht_plan* plan, int64_t nrhs, int64_t* l
   });
 }
 
+mht_status mht_synthesize_noalloc(const mht_plan* plan, const void* factor_dev, const void* c_dev, void* f_dev,
+                                  void* stream) {
+  return guarded([&]() -> mht_status {
+    if (!plan || !factor_dev || !c_dev || !f_dev) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(factor_dev) & 255) mht::fail(MHT_ERR_INVALID_ARG, "factor_dev must be 256-byte aligned");
+    std::string err;
+    int rc = mht::apply_synthesize_noalloc(plan->P, factor_dev, c_dev, f_dev, stream, err);
+    return rc ? set_error(mht_status(rc), err) : MHT_OK;
+  });
+}
+
 mht_status mht_plan_check(mht_plan* plan, void* stream, int32_t* flags) {
   return guarded([&]() -> mht_status {
     if (!plan || !flags) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");

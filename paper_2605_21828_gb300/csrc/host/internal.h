@@ -160,6 +160,9 @@ int device_upload(void* dst, const void* src, size_t bytes, void* stream, std::s
 int device_copy_async(void* dst, const void* src, size_t bytes, int kind, void* stream,
                       std::string& err);
 int device_sync(void* stream, std::string& err);
+// Fused FP32 synthesis of one vector with scratch from a fixed library array (no allocation).
+int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void* c, void* f, void* stream,
+                             std::string& err);
 // Copies the device status word to *flags, clears it, and synchronizes the stream.
 int device_status(void* status_dev, void* stream, unsigned* flags, std::string& err);
 }  // namespace mht
