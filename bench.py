@@ -42,10 +42,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--multi-rhs", type=int, default=64, help="extra measurement at this many RHS (0: off)")
-    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64"],
+                    help="batch64: 64 ragged instances (torus / sphere / deformed sphere, n in [2000, 40000], "
+                         "m = n/4, 1-128 RHS each) in one persistent launch per direction")
     ap.add_argument("--plan-cache", default=os.environ.get("MHT_PLAN_CACHE", ""))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the FP64 error check of the multi-RHS forms")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default launch shapes")
+    ap.add_argument("--path", default="auto", choices=["auto", "fused", "staged"],
+                    help="apply path: one persistent launch per direction, or one launch per stage")
     return ap.parse_args()
 
 
@@ -102,6 +108,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload not in WORKLOADS:
+        raise SystemExit("--impl reference times the oracle on the single-plan workloads only")
     desc = workload_desc(args.workload)
     steps = max(1, args.steps)
     for _ in range(max(0, args.warmup)):
@@ -214,6 +222,15 @@ def run_ours(args):
     nrhs = args.nrhs
     max_nrhs = max(nrhs, args.multi_rhs or 1)
     plan.bind(device=dev, max_nrhs=max_nrhs)
+    plan.set_path(args.path)
+    tune = None
+    if not args.no_autotune and args.path != "fused":
+        t0 = time.time()
+        cfgs = plan.autotune(nrhs)
+        tune = {"seconds": round(time.time() - t0, 2),
+                "stages [dir, stage, tensor, rhs_tile, slot_KB, slots, CTAs/SM]": [
+                    [t["direction"], t["stage"], t["tensor"], t["rhs_tile"], t["slot_kb"], t["slots"],
+                     t["ctas_per_sm"]] for t in cfgs]}
     n, m = plan.n, plan.m
     c = torch.from_numpy(W.sphere_coefficients(m, nrhs)).float().to(dev)
     c = c[:, 0].contiguous() if nrhs == 1 else c
@@ -232,10 +249,12 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")  # profilers can select these launches
     ev0.record(stream)
     for _ in range(K):
         step(c)
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -260,46 +279,35 @@ def run_ours(args):
     # per-stage roofline: the dominant kernel is the one with the most device time
     L = plan.levels
     stages = [plan.level_info(s) for s in range(L + 2)]
+    all_bytes = sum(st_["algorithmic_bytes"] for st_ in stages)  # one fused launch runs every stage
     kern = {
-        "k_synth (transfer levels 0..L)": (syn_ms[:L + 1].sum(), syn_n[:L + 1].sum(),
-                                           sum(stages[s]["algorithmic_bytes"] * syn_n[s] for s in range(L + 1))),
-        "k_adjoint (transfer levels L..0)": (adj_ms[:L + 1].sum(), adj_n[:L + 1].sum(),
-                                             sum(stages[s]["algorithmic_bytes"] * adj_n[s] for s in range(L + 1))),
-        "k_synth (column bases U)": (syn_ms[L + 1], syn_n[L + 1], stages[L + 1]["algorithmic_bytes"] * syn_n[L + 1]),
-        "k_adjoint (column bases U)": (adj_ms[L + 1], adj_n[L + 1], stages[L + 1]["algorithmic_bytes"] * adj_n[L + 1]),
+        "k_rowdot synthesis (transfer levels 0..L)": (
+            syn_ms[:L + 1].sum(), syn_n[:L + 1].sum(),
+            sum(stages[s]["algorithmic_bytes"] * syn_n[s] for s in range(L + 1))),
+        "k_rowdot adjoint (transfer levels L..0)": (
+            adj_ms[:L + 1].sum(), adj_n[:L + 1].sum(),
+            sum(stages[s]["algorithmic_bytes"] * adj_n[s] for s in range(L + 1))),
+        "k_rowdot synthesis (column bases U)": (syn_ms[L + 1], syn_n[L + 1],
+                                                stages[L + 1]["algorithmic_bytes"] * syn_n[L + 1]),
+        "k_rowdot adjoint (column bases U)": (adj_ms[L + 1], adj_n[L + 1],
+                                              stages[L + 1]["algorithmic_bytes"] * adj_n[L + 1]),
+        "k_fused synthesis (all stages, one launch)": (syn_ms[L + 2], syn_n[L + 2], all_bytes * syn_n[L + 2]),
+        "k_fused adjoint (all stages, one launch)": (adj_ms[L + 2], adj_n[L + 2], all_bytes * adj_n[L + 2]),
     }
     name, (kms, kl, kbytes) = max(kern.items(), key=lambda kv: kv[1][0])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = (kbytes / 1e9) / (kms / 1e3) if kms > 0 else 0.0
-    step_bytes = sum(stages[s]["algorithmic_bytes"] * (syn_n[s] + adj_n[s]) for s in range(L + 2)) / K
+    step_bytes = 2 * all_bytes  # one synthesis + one adjoint (factor bytes dominate)
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else
                 "fallback 6800 GB/s", "traffic": None, "launches": int(kl), "avg_launch_ms": kms / max(kl, 1),
                 "step_algorithmic_GB": step_bytes / 1e9,
                 "step_frac": (step_bytes / 1e9) / (ms_step / 1e3) / peak}
-    per_stage = {"synth_ms": [round(x / K, 5) for x in syn_ms], "adjoint_ms": [round(x / K, 5) for x in adj_ms],
+    per_stage = {"path": args.path, "launches_per_step": int((syn_n.sum() + adj_n.sum()) // K),
+                 "synth_ms": [round(x / K, 5) for x in syn_ms], "adjoint_ms": [round(x / K, 5) for x in adj_ms],
                  "algorithmic_MB": [round(s["algorithmic_bytes"] / 1e6, 3) for s in stages]}
-
-    # multi-RHS measurement (same step, more vectors per launch)
-    multi = None
-    if args.multi_rhs and args.multi_rhs > 1:
-        km = args.multi_rhs
-        C = torch.from_numpy(W.sphere_coefficients(m, km)).float().to(dev)
-        for _ in range(3):
-            step(C)
-        torch.cuda.synchronize()
-        reps = max(3, K // 4)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            step(C)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        mms = e0.elapsed_time(e1) / reps
-        multi = {"nrhs": km, "ms_per_step": mms, "transforms_per_s": world * km / (mms / 1e3),
-                 "mode": "fp32 SIMT"}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
@@ -335,6 +343,55 @@ def run_ours(args):
                "h2d_bytes_per_step": (m + n) * 4 * nrhs, "d2h_bytes_per_step": (n + m) * 4 * nrhs,
                "api": "mht_synthesize_host + mht_analyze_host (pinned host buffers)"}
 
+    # multi-RHS measurement (same step, more vectors per launch): plain FP32 SIMT products
+    # against the 3xTF32 tensor-core products, with the relative difference of their results
+    multi = None
+    if args.multi_rhs and args.multi_rhs > 1:
+        km = args.multi_rhs
+        plan.set_path("auto")  # wide RHS counts take the per-stage kernels
+        C = torch.from_numpy(W.sphere_coefficients(m, km)).float().to(dev)
+        multi = {"nrhs": km}
+        outs = {}
+        for mode in ("fp32", "3xtf32"):
+            plan.set_mode(mode)
+            if not args.no_autotune:
+                plan.autotune(km)
+            for _ in range(3):
+                step(C)
+            torch.cuda.synchronize()
+            reps = max(3, K // 4)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                step(C)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mms = e0.elapsed_time(e1) / reps
+            outs[mode] = (plan.synthesize_raw(C), step(C))
+            multi[mode] = {"ms_per_step": mms, "transforms_per_s": world * km / (mms / 1e3)}
+        plan.set_mode("fp32")
+        multi["fp32"]["kernels"] = "k_rowdot (SIMT FP32)"
+        multi["3xtf32"]["kernels"] = "k_tc3 (tcgen05 kind::tf32, 3 products per k-step)"
+        for i, nm in enumerate(("synthesis", "round_trip")):
+            a_, b_ = outs["fp32"][i].double(), outs["3xtf32"][i].double()
+            multi[f"rel_diff_{nm}"] = float(torch.linalg.norm(a_ - b_) / torch.linalg.norm(a_))
+        multi["speedup_3xtf32_vs_fp32"] = multi["fp32"]["ms_per_step"] / multi["3xtf32"]["ms_per_step"]
+        if not args.no_accuracy:
+            # rounding error of both FP32 forms against the FP64 apply of the same factors
+            # (max over RHS of the relative l2 error per RHS)
+            ref = plan.clone("fp64").bind(device=dev, max_nrhs=km)
+            C64 = C.double()
+            r_syn = ref.synthesize_raw(C64)
+            r_rt = ref.analyze_raw(r_syn, weighted=True)
+            torch.cuda.synchronize()
+            for mode in ("fp32", "3xtf32"):
+                for i, (nm, r) in enumerate((("synthesis", r_syn), ("round_trip", r_rt))):
+                    e = torch.linalg.norm(outs[mode][i].double() - r, dim=0) / torch.linalg.norm(r, dim=0)
+                    multi[mode][f"rel_err_{nm}_vs_fp64"] = float(e.max())
+            ref.close()
+            del ref, r_syn, r_rt, C64
+            torch.cuda.empty_cache()
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, meta, _ = cpu_baseline(args.workload, budget_s=15.0)
@@ -350,6 +407,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": desc, "roofline": roofline, "per_stage": per_stage,
             "multi_rhs": multi, "e2e": e2e, "cpu_baseline": cb, "clocks": clk, "gpu_launches": launches,
+            "autotune": tune,
             "device_status": status}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -357,10 +415,149 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def batch_plans(args):
+    """The 64 instances of the batched ragged workload (built once, cached as plan files)."""
+    import numpy as np
+
+    import workloads as W
+    from paper_2605_21828_gb300 import Plan
+    specs = W.batched_instances(64, seed=2)
+    cache = args.plan_cache or os.path.join(tempfile.gettempdir(), "mht_batch64")
+    os.makedirs(cache, exist_ok=True)
+    plans, t0, built = [], time.time(), 0
+    for i, sp in enumerate(specs):
+        path = os.path.join(cache, f"inst{i:02d}.plan")
+        n, m = sp["n"], sp["m"]
+        if os.path.exists(path):
+            plans.append(Plan.load(path, mode="fp32"))
+            continue
+        kw = dict(n=n, m=m, eps=1e-6, leaf_size=64, mode="fp32")
+        if sp["kind"] == "torus":
+            K = W.torus_modes_lowest(m)
+            p = Plan.build(eigenvalues=W.torus_eigenvalues(K), evaluator="torus", points=W.torus_points(n, seed=i),
+                           torus_modes=K, weights=np.full(n, 4 * np.pi ** 2 / n), **kw)
+        else:
+            X = W.fibonacci_points(n, seed=i) if sp["kind"] == "sphere" else W.deformed_sphere_points(n, seed=i)
+            p = Plan.build(eigenvalues=W.sphere_eigenvalues(m), evaluator="sphere", points=X,
+                           weights=np.full(n, 4 * np.pi / n), **kw)
+        p.save(path)
+        plans.append(p)
+        built += 1
+    return specs, plans, time.time() - t0, built
+
+
+def run_batch(args):
+    """Batched ragged workload: one persistent launch per direction (CUDA graph) for all 64
+    instances, against the plain FP32 per-instance apply (one mht_synthesize / mht_analyze
+    per instance) on the same inputs."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2605_21828_gb300 import Batch
+    from paper_2605_21828_gb300.build import build_library
+    build_library()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs, plans, setup_s, built = batch_plans(args)
+    ks = [sp["nrhs"] for sp in specs]
+    total_rhs = sum(ks)
+    bt = Batch(plans, ks).bind(device=dev)
+    for i, p in enumerate(plans):
+        C_ = W.gaussian_columns(p.m, ks[i], 100 + i, complex_=p.complex)
+        bt.c[i].copy_(torch.from_numpy(C_).to(bt.c[i].dtype))
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.time()
+    tune_ms = bt.autotune() if not args.no_autotune else None
+    tune_s = time.time() - t0
+    for i, p in enumerate(plans):  # the autotuner overwrote the vectors
+        C_ = W.gaussian_columns(p.m, ks[i], 100 + i, complex_=p.complex)
+        bt.c[i].copy_(torch.from_numpy(C_).to(bt.c[i].dtype))
+
+    def step():
+        bt.synthesize()
+        bt.analyze(weighted=True)
+
+    clocks = ClockSampler()
+    clocks.start()
+    K, Wm = args.steps, max(args.warmup, 3)
+    for _ in range(Wm):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    status = bt.check()
+    f_batch = [f.clone() for f in bt.synthesize()]
+    c_batch = [c.clone() for c in bt.analyze(weighted=True)]
+
+    # plain FP32 per-instance apply of the same vectors (per-stage kernels, one call per instance)
+    for p, k in zip(plans, ks):
+        p.bind(device=dev, max_nrhs=k).set_path("staged")
+    cin = [bt.c[i].clone() for i in range(len(plans))]
+    for i in range(len(plans)):
+        bt.c[i].copy_(cin[i])
+
+    def step_plain():
+        for i, p in enumerate(plans):
+            f = p.synthesize_raw(cin[i])
+            p.analyze_raw(f, weighted=True)
+
+    for _ in range(Wm):
+        step_plain()
+    torch.cuda.synchronize()
+    reps = max(3, K // 4)
+    e0.record(stream)
+    for _ in range(reps):
+        step_plain()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1) / reps
+    clk = clocks.stop(0)
+    # the batch and the per-instance apply run the same row arithmetic: compare exactly
+    same = all(torch.equal(p.synthesize_raw(cin[i]).reshape(f_batch[i].shape), f_batch[i])
+               for i, p in enumerate(plans))
+
+    factor_bytes = sum(2 * sum(p.level_info(s)["algorithmic_bytes"] for s in range(p.levels + 2)) for p in plans)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = factor_bytes / 1e9 / (ms / 1e3)
+    info = bt.info()
+    line = {"metric": "transforms/s (synthesis + weighted adjoint), batched ragged", "value": total_rhs / (ms / 1e3),
+            "unit": "transforms/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched ragged: 64 instances cycling flat torus / unit sphere / deformed sphere, "
+                                   "n uniform in [2000, 40000] (seed 2), m = n/4, 1-128 RHS each, eps=1e-6, leaf 64",
+                       "instances": len(plans), "total_rhs": total_rhs, "n_total": sum(sp["n"] for sp in specs),
+                       "factor_GB": sum(p.info()["factor_bytes"] for p in plans) / 1e9,
+                       "items_per_direction": [info["items_synthesis"], info["items_analysis"]],
+                       "persistent_ctas": info["grid"], "plan_setup_s": round(setup_s, 1), "plans_built_here": built,
+                       "deformed_basis": "spherical harmonics of the radial direction at deformed-sphere points",
+                       "l2": "factors (GBs) > 129 MB L2"},
+            "per_instance_fp32": {"ms_per_step": ms_plain, "transforms_per_s": total_rhs / (ms_plain / 1e3),
+                                  "launches_per_step": 2 * sum(p.levels + 2 for p in plans),
+                                  "identical_results": bool(same)},
+            "speedup_vs_per_instance": ms_plain / ms,
+            "roofline": {"bound": "hbm", "kernel": "k_batch (both directions, all instances)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "note": "factor and index bytes read once per step; RHS tiles beyond the "
+                                                  "first re-read an item's rows from L2"},
+            "autotune": {"seconds": round(tune_s, 2), "best_ms_both_directions": tune_ms},
+            "gpu_launches": 2 * (K + Wm), "clocks": clk, "device_status": status}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct mht_plan mht_plan;
+typedef struct mht_batch mht_batch;
 
 typedef enum {
   MHT_OK = 0,
@@ -198,6 +199,11 @@ mht_status mht_build_plan(const mht_problem* problem, const mht_options* options
 mht_status mht_plan_import(const mht_factors* factors, const mht_options* options,
                            mht_plan** out);
 
+/* Creates an independent plan with the same factors as `src`, packed for options->mode (for
+ * example an FP64 plan beside an FP32 one, to measure the FP32 rounding error of an apply).
+ * The copy is unbound.  Errors: INVALID_ARG. */
+mht_status mht_plan_clone(const mht_plan* src, const mht_options* options, mht_plan** out);
+
 /* Copies the plan's FP64 factors into caller arrays sized from mht_plan_info (scalar
  * fields of *factors are filled in; array pointers may be NULL to skip an array). */
 mht_status mht_plan_export(const mht_plan* plan, mht_factors* factors);
@@ -278,11 +284,34 @@ mht_status mht_synthesize_noalloc(const mht_plan* plan, const void* factor_dev, 
  * every wait since the last check completed, MHT_ERR_TIMEOUT (and the flags) otherwise. */
 mht_status mht_plan_check(mht_plan* plan, void* stream, int32_t* flags);
 
-/* Apply path: 0 = automatic (one persistent launch per direction that runs every stage
- * when up to 8 RHS fit its shared memory, otherwise one launch per stage), 1 = always one
- * launch per stage, 2 = always the persistent launch (MHT_ERR_UNSUPPORTED if it does not
- * fit).  Both paths compute the same result. */
+/* Apply path: 0 = automatic (currently one launch per stage, the faster path on the
+ * measured workloads), 1 = one launch per stage, 2 = one persistent launch per direction that
+ * runs every stage (up to 8 RHS; MHT_ERR_UNSUPPORTED if it does not fit).  Both paths compute
+ * the same result. */
 mht_status mht_plan_set_path(mht_plan* plan, int32_t path);
+
+/* Switches the arithmetic of later applies between MHT_APPLY_FP32 and MHT_APPLY_3XTF32 on a
+ * plan whose factors are stored in float (both modes read the same packed image, so no
+ * rebinding is needed).  MHT_ERR_INVALID_ARG for an FP64 plan or for MHT_APPLY_FP64, whose
+ * storage precision differs.  The block products of the apply (Sec. 2) with a block of
+ * vectors take the tensor-core path only in MHT_APPLY_3XTF32 and from 16 real (8 complex)
+ * RHS on; complex products run as real products of twice the width. */
+mht_status mht_plan_set_mode(mht_plan* plan, mht_apply_mode mode);
+
+/* Autotuner: times the candidate launch configurations of every stage of both directions
+ * for `nrhs` right-hand sides (SIMT RHS tile 1/2/4/8, bulk-copy ring of 1-8 slots of 16/32/64
+ * KB, resident CTAs per SM, and in MHT_APPLY_3XTF32 mode the tensor-core kernel) on the bound
+ * workspace, and
+ * keeps the fastest per stage; later applies with exactly `nrhs` RHS use them (others use the
+ * defaults).  Runs the stages on zeroed workspace buffers only (the caller's vectors are not
+ * touched) and synchronizes `stream`; takes about a second on a 15 GB plan.  Results equal
+ * the untuned apply's within rounding (RHS tile and kernel change the summation order).
+ * Errors: INVALID_ARG (nrhs < 1 or > the bound max_nrhs), NOT_BOUND, CUDA. */
+mht_status mht_plan_autotune(mht_plan* plan, int64_t nrhs, void* stream);
+/* The tuned configuration of one stage (direction 0 synthesis / 1 analysis; stage 0..L+1):
+ * cfg[5] = {tensor cores (0/1), RHS tile, ring slots, CTAs per SM, slot KB} (0 = the default)
+ * and its measured milliseconds.  INVALID_ARG if the plan has not been tuned. */
+mht_status mht_plan_tune_info(const mht_plan* plan, int32_t direction, int32_t stage, int32_t* cfg, double* ms);
 
 /* Stage timing for benchmarks.  While enabled, every apply on the plan records a CUDA
  * event before and after each kernel launch (on the apply's stream).
@@ -293,6 +322,49 @@ mht_status mht_plan_set_path(mht_plan* plan, int32_t path);
  * launch; disabled (the default) it costs nothing. */
 mht_status mht_plan_profile(mht_plan* plan, int32_t enable);
 mht_status mht_plan_stage_times(mht_plan* plan, int32_t direction, double* ms, int64_t* launches);
+
+/* ---- batched ragged apply ---------------------------------------------------------------
+ * Many FP32 plans (instances of different n, m, depth L, real or complex) and their RHS
+ * counts applied together: every stage of every instance runs in ONE persistent kernel
+ * launch per direction, replayed from a CUDA graph (a counter reset and the kernel).  Work
+ * items of all instances share one queue in dependency order (the phases of Sec. 2's apply:
+ * V, then R for l = 1..L, then U, per instance; the adjoint in reverse), so small instances
+ * and the tails of large stages overlap instead of each paying a launch and a drain.
+ * Results equal the per-plan mht_synthesize / mht_analyze (same kernels' arithmetic).
+ *
+ * Lifecycle: mht_batch_create (host only; the plans must stay alive until
+ * mht_batch_bind_device returns) -> mht_batch_device_bytes -> mht_batch_bind_device
+ * (uploads the packed factors into caller memory, synchronous) -> mht_batch_set_io (fixes
+ * the caller's device vectors: c_i column-major m_i x nrhs_i with leading dimension ldc[i],
+ * f_i n_i x nrhs_i with ldf[i]; complex instances use interleaved float pairs) ->
+ * mht_batch_synthesize / mht_batch_analyze (asynchronous on `stream`) -> mht_batch_destroy.
+ * Calls on one batch must not overlap on the GPU (they share the workspace).
+ * Errors: INVALID_ARG (NULL, count <= 0, FP64 plan, bad RHS count or leading dimension),
+ * NOT_BOUND, UNSUPPORTED (a block too wide for shared memory), CUDA. */
+mht_status mht_batch_create(mht_plan* const* plans, int32_t count, const int64_t* nrhs, mht_batch** out);
+mht_status mht_batch_device_bytes(const mht_batch* batch, size_t* image_bytes, size_t* workspace_bytes);
+mht_status mht_batch_bind_device(mht_batch* batch, void* image_dev, size_t image_bytes, void* workspace_dev,
+                                 size_t workspace_bytes, void* stream);
+mht_status mht_batch_set_io(mht_batch* batch, void* const* c_dev, const int64_t* ldc, void* const* f_dev,
+                            const int64_t* ldf, void* stream);
+/* f_i = Phi_i c_i for every instance. */
+mht_status mht_batch_synthesize(mht_batch* batch, void* stream);
+/* c_i = Phi_i^H W_i f_i (weighted != 0) or Phi_i^H f_i for every instance. */
+mht_status mht_batch_analyze(mht_batch* batch, int32_t weighted, void* stream);
+/* 1 (default): launches replay CUDA graphs; 0: plain stream launches (same work). */
+mht_status mht_batch_set_graph(mht_batch* batch, int32_t use_graph);
+/* Work items per direction and CTAs of one persistent launch (needs a current device). */
+mht_status mht_batch_info(const mht_batch* batch, int64_t* items_synthesis, int64_t* items_analysis,
+                          int32_t* grid);
+/* Reads and clears the batch's device status word (synchronizes `stream`); TIMEOUT if a
+ * bounded wait gave up (bit 0: a bulk copy, bit 1: a dependency). */
+mht_status mht_batch_check(mht_batch* batch, void* stream, int32_t* flags);
+/* Autotuner of the batched launch: times one synthesis + analysis for every (ring slots,
+ * resident CTAs per SM) pair that fits and keeps the fastest for later launches (the CUDA
+ * graphs are rebuilt).  Overwrites the batch's f and c vectors; synchronizes `stream`;
+ * *best_ms (optional) receives the time of the chosen pair for both directions. */
+mht_status mht_batch_autotune(mht_batch* batch, void* stream, double* best_ms);
+mht_status mht_batch_destroy(mht_batch* batch);
 
 /* ---- persistence and lifetime -------------------------------------------------------- */
 

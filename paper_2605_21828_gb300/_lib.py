@@ -84,8 +84,24 @@ SIGNATURES = {
     "mht_plan_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "mht_synthesize_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mht_plan_set_path": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mht_plan_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "mht_plan_clone": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mht_plan_autotune": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "mht_plan_tune_info": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "mht_plan_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "mht_plan_stage_times": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "mht_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_void_p)]),
+    "mht_batch_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "mht_batch_bind_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "mht_batch_set_io": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_int64), C.c_void_p]),
+    "mht_batch_synthesize": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mht_batch_analyze": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "mht_batch_set_graph": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mht_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "mht_batch_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "mht_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "mht_batch_destroy": (C.c_int, [C.c_void_p]),
     "mht_plan_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mht_plan_load": (C.c_int, [C.c_char_p, C.POINTER(Options), C.POINTER(C.c_void_p)]),
     "mht_destroy": (C.c_int, [C.c_void_p]),

@@ -166,6 +166,12 @@ class Plan:
         L.check(L.load().mht_plan_load(path.encode(), C.byref(_options(mode=mode)), C.byref(h)))
         return Plan(h, mode)
 
+    def clone(self, mode: str = "fp64") -> "Plan":
+        """An unbound copy of the same factors, packed for another apply mode."""
+        h = C.c_void_p()
+        L.check(L.load().mht_plan_clone(self._h, C.byref(_options(mode=mode)), C.byref(h)))
+        return Plan(h, mode)
+
     def save(self, path: str):
         L.check(L.load().mht_plan_save(self._h, path.encode()))
 
@@ -227,6 +233,28 @@ class Plan:
         L.check(L.load().mht_plan_set_path(self._h, {"auto": 0, "staged": 1, "fused": 2}[path]))
         return self
 
+    def set_mode(self, mode: str):
+        """'fp32' or '3xtf32' on a float plan (same packed factors, no rebinding)."""
+        L.check(L.load().mht_plan_set_mode(self._h, _MODES[mode]))
+        self.mode = mode
+        return self
+
+    def autotune(self, nrhs: int = 1):
+        """Times each stage's candidate launch configurations for ``nrhs`` RHS and keeps the
+        fastest (used by later applies with exactly ``nrhs`` RHS); returns the choices."""
+        import torch
+        s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        L.check(L.load().mht_plan_autotune(self._h, int(nrhs), s))
+        out = []
+        cfg = (C.c_int32 * 5)()
+        ms = C.c_double()
+        for d in (0, 1):
+            for st in range(self.levels + 2):
+                if L.load().mht_plan_tune_info(self._h, d, st, cfg, C.byref(ms)) == 0:
+                    out.append({"direction": d, "stage": st, "tensor": cfg[0], "rhs_tile": cfg[1],
+                                "slots": cfg[2], "ctas_per_sm": cfg[3], "slot_kb": cfg[4], "ms": ms.value})
+        return out
+
     def profile(self, enable: bool = True):
         L.check(L.load().mht_plan_profile(self._h, 1 if enable else 0))
 
@@ -242,6 +270,7 @@ class Plan:
         if self._h:
             L.load().mht_destroy(self._h)
             self._h = None
+        self._dev = None  # releases the device buffers this plan allocated
 
     def __del__(self):
         try:
@@ -370,6 +399,109 @@ def _autograd():
 
 
 _AG = None
+
+
+class Batch:
+    """Many FP32 plans applied together: one persistent launch per direction (CUDA graph).
+
+    ``c[i]`` (m_i x k_i) and ``f[i]`` (n_i x k_i) are device tensors owned by the batch
+    (column-major views); fill ``c`` and call :meth:`synthesize`, or fill ``f`` and call
+    :meth:`analyze`.  The plans must stay alive until :meth:`bind` returns.
+    """
+
+    def __init__(self, plans, nrhs):
+        lib = L.load()
+        n = len(plans)
+        if n == 0 or len(nrhs) != n:
+            raise ValueError("need one RHS count per plan")
+        hs = (C.c_void_p * n)(*[p._h for p in plans])
+        ks = (C.c_int64 * n)(*[int(k) for k in nrhs])
+        h = C.c_void_p()
+        L.check(lib.mht_batch_create(hs, n, ks, C.byref(h)))
+        self._h = h
+        self._plans = list(plans)
+        self.nrhs = [int(k) for k in nrhs]
+        self.shapes = [(p.n, p.m, p.complex) for p in plans]
+        self._dev = None
+        self.c = self.f = None
+
+    def device_bytes(self):
+        ib, wb = C.c_size_t(), C.c_size_t()
+        L.check(L.load().mht_batch_device_bytes(self._h, C.byref(ib), C.byref(wb)))
+        return int(ib.value), int(wb.value)
+
+    def bind(self, device="cuda"):
+        import torch
+        lib = L.load()
+        ib, wb = self.device_bytes()
+        img = torch.empty(ib + 256, dtype=torch.uint8, device=device)
+        ws = torch.empty(wb + 256, dtype=torch.uint8, device=device)
+        ip = (img.data_ptr() + 255) // 256 * 256
+        wp = (ws.data_ptr() + 255) // 256 * 256
+        stream = C.c_void_p(torch.cuda.current_stream(img.device).cuda_stream)
+        L.check(lib.mht_batch_bind_device(self._h, C.c_void_p(ip), ib, C.c_void_p(wp), wb, stream))
+        self._plans = None  # factors are on the device now
+        cs, fs = [], []
+        for (n, m, cplx), k in zip(self.shapes, self.nrhs):
+            dt = torch.complex64 if cplx else torch.float32
+            cs.append(torch.zeros((k, m), dtype=dt, device=img.device))
+            fs.append(torch.zeros((k, n), dtype=dt, device=img.device))
+        nb = len(cs)
+        cp = (C.c_void_p * nb)(*[t.data_ptr() for t in cs])
+        fp = (C.c_void_p * nb)(*[t.data_ptr() for t in fs])
+        ldc = (C.c_int64 * nb)(*[m for (_, m, _) in self.shapes])
+        ldf = (C.c_int64 * nb)(*[n for (n, _, _) in self.shapes])
+        L.check(lib.mht_batch_set_io(self._h, cp, ldc, fp, ldf, stream))
+        self._dev = (img, ws, cs, fs)
+        self.c = [t.t() for t in cs]  # m x k views of the column-major buffers
+        self.f = [t.t() for t in fs]
+        return self
+
+    def _stream(self):
+        import torch
+        return C.c_void_p(torch.cuda.current_stream(self._dev[0].device).cuda_stream)
+
+    def synthesize(self):
+        """f[i] = Phi_i c[i] for every instance (one launch); returns the list f."""
+        L.check(L.load().mht_batch_synthesize(self._h, self._stream()))
+        return self.f
+
+    def analyze(self, weighted: bool = True):
+        """c[i] = Phi_i^H W_i f[i] (or without W) for every instance; returns the list c."""
+        L.check(L.load().mht_batch_analyze(self._h, 1 if weighted else 0, self._stream()))
+        return self.c
+
+    def autotune(self):
+        """Picks the fastest (ring slots, CTAs per SM) for this batch; overwrites f and c."""
+        ms = C.c_double()
+        L.check(L.load().mht_batch_autotune(self._h, self._stream(), C.byref(ms)))
+        return ms.value
+
+    def set_graph(self, use_graph: bool = True):
+        L.check(L.load().mht_batch_set_graph(self._h, 1 if use_graph else 0))
+        return self
+
+    def info(self):
+        a, b, g = C.c_int64(), C.c_int64(), C.c_int32()
+        L.check(L.load().mht_batch_info(self._h, C.byref(a), C.byref(b), C.byref(g)))
+        return {"items_synthesis": int(a.value), "items_analysis": int(b.value), "grid": int(g.value)}
+
+    def check(self):
+        f = C.c_int32()
+        L.check(L.load().mht_batch_check(self._h, self._stream(), C.byref(f)))
+        return int(f.value)
+
+    def close(self):
+        if self._h:
+            L.load().mht_batch_destroy(self._h)
+            self._h = None
+        self._dev = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 def synthesize(plan: Plan, c):

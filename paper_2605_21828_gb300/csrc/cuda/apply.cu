@@ -10,12 +10,13 @@
 // once per apply (apply cost equals storage, Sec. 6.2), so the single-RHS apply is bound by
 // HBM bandwidth.  The packed plan holds every matrix in both orientations, so both
 // directions are "rows times a gathered vector":
-//   * one CTA per work item (block, row range of ~32 KB);
-//   * thread 0 stages the item's rows into shared memory with one 1-D TMA bulk copy
-//     (cp.async.bulk, completion on an mbarrier) while all threads gather the block's
-//     input vector from L2 into shared memory;
-//   * each warp then reduces whole rows from shared memory with 128-bit loads and warp
-//     shuffles.
+//   * k_rowdot: one persistent launch per stage; each CTA takes work items (block, row range
+//     of ~128 KB) in a fixed stride, and thread 0 keeps a ring of 32 KB shared-memory slots
+//     filled by 1-D TMA bulk copies (cp.async.bulk, completion on mbarriers) across item
+//     boundaries, while all threads gather the block's input vector from L2;
+//   * each warp then reduces whole rows from shared memory with 128-bit loads, compensated
+//     FP32 sums and warp shuffles (building blocks in rowdot.cuh);
+//   * k_fused: one persistent launch for all stages with per-block completion counters.
 // The adjoint is a gather: the sibling blocks (2p, nu), (2p+1, nu) that share an input pair
 // write separate buffers and the next stage sums them while loading -- no atomics, so the
 // result is deterministic.  Every mbarrier wait is bounded; on timeout the kernel sets a bit
@@ -28,248 +29,37 @@
 #include <vector>
 
 #include "../host/internal.h"
+#include "rowdot.cuh"
 
 namespace mht {
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits give up after 2 s
-
-enum Mode { SYN_ID = 0, ADJ_ID = 1, SYN_U = 2, ADJ_U = 3 };
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for the phase with the given parity; gives up after kWaitNs of wall time, or as soon
-// as *abort_flag is non-zero (when given).  Returns false when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase,
-                                                  const unsigned* abort_flag = nullptr) {
-  if (mbar_try_wait(bar, phase)) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  for (unsigned it = 1;; ++it) {
-    if (mbar_try_wait(bar, phase)) return true;
-    if ((it & 255) == 0) {
-      if (globaltimer_ns() - t0 > kWaitNs) return false;
-      if (abort_flag && *reinterpret_cast<const volatile unsigned*>(abort_flag) != 0u) return false;
-    }
-  }
-}
-
-template <class R>
-struct alignas(16) Vec16 {  // one 128-bit load / store
-  static constexpr int NS = 16 / sizeof(R);
-  R s[NS];
-};
-
-template <class R>
-__device__ __forceinline__ R warp_sum(R v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// ---------------------------------------------------------------------------------------
-// out[o(i)] = ident(i) + sum_j M[i, j] x[j] for the rows i of one work item.
-//   SYN_ID: M = T~ (r x K'),           x[j] = in[idx[r + j]],   o(i) = out_off + i,
-//           ident(i) = in[idx[i]]
-//   ADJ_ID: M = conj(T~)^T (K' x r),   x[j] = z0[out_off + j] (+ z1[...]),
-//           o(i) = idx[r + i] in the sibling buffer; skeleton out[idx[j]] = x[j]
-//   SYN_U:  M = U (|tau| x r_L),       x[j] = yL[in_off + j],   o(i) = perm[out_off + i]
-//           (times w[o(i)] when weights are given)
-//   ADJ_U:  M = conj(U)^T (r_L x |tau|), x[j] = w[p] f[p] with p = perm[out_off + j],
-//           o(i) = in_off + i
-// Element strides: in[e * is_e + k * is_k], out[e * os_e + k * os_k]; one complex value is
-// one element.  RT right-hand sides per CTA (blockIdx.y selects the RHS tile).
+// One launch per stage and direction, persistent: CTA b computes items b, b + gridDim.x, ...
 template <class R, bool C, int RT, int MODE>
 __global__ void __launch_bounds__(kThreads)
-k_rowdot(const R* __restrict__ data, const int* __restrict__ idx, const MhtBlockDesc* __restrict__ desc,
-         const MhtItem* __restrict__ items, const int* __restrict__ perm, const R* __restrict__ wts,
-         const R* __restrict__ in0, const R* __restrict__ in1, long long is_e, long long is_k,
-         R* __restrict__ out0, R* __restrict__ out1, long long os_e, long long os_k, int nrhs,
-         int tile_bytes_max, int ldx_max, unsigned* __restrict__ status) {
-  constexpr int W = C ? 2 : 1;
-  constexpr int NS = 16 / sizeof(R);
-  constexpr int E = NS / W;
+k_rowdot(RowArgs<R> a, const MhtItem* __restrict__ items, int nitems, int slot_bytes, int nslot, int ldx_max,
+         int rows_max, unsigned* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  R* tile = reinterpret_cast<R*>(smem_raw + 128);
-  R* xs = reinterpret_cast<R*>(smem_raw + 128 + ((tile_bytes_max + 127) / 128) * 128);  // [RT][ldx][W]
-
-  const MhtItem it = items[blockIdx.x];
-  const MhtBlockDesc d = desc[it.blk];
-  const int k0 = blockIdx.y * RT;
-  const int nk = min(RT, nrhs - k0);
-  const int ldt = d.ldt;
-  const unsigned bytes = unsigned(it.count) * unsigned(ldt) * unsigned(W * sizeof(R));
-  R* out = (MODE == ADJ_ID && it.sib) ? out1 : out0;
-
-  if (threadIdx.x == 0) mbar_init(bar, 1);
-  __syncthreads();
-  if (threadIdx.x == 0 && bytes > 0) {
-    mbar_expect_tx(bar, bytes);
-    bulk_copy_g2s(tile, data + (d.t_off + (long long)it.start * ldt) * W, bytes, bar);
-  }
-
-  // gather the input vector while the tile is in flight (zero padding to ldt and beyond nk)
-  for (int j = threadIdx.x; j < ldt; j += kThreads) {
-    long long src = -1;
-    R w = R(1);
-    if (j < d.cols) {
-      if (MODE == SYN_ID) src = idx[d.idx_off + d.rows + j];
-      else if (MODE == ADJ_ID) src = (long long)d.out_off + j;
-      else if (MODE == SYN_U) src = (long long)d.in_off + j;
-      else {
-        src = perm[d.out_off + j];
-        if (wts) w = wts[src];
-      }
+  const RowSmem sm = row_smem<R, C>(smem_raw, slot_bytes, nslot, ldx_max, rows_max);
+  RowProducer<R, C> prod{items, a.desc, a.data, nitems, int(gridDim.x), (a.nrhs + RT - 1) / RT, int(blockIdx.x)};
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nslot; ++i) mbar_init(&sm.bar[i], 1);
+    *sm.flag = 1;
+    prod.load(slot_bytes);
+    while (prod.issued < unsigned(nslot) && prod.issue(sm)) {
     }
-#pragma unroll
-    for (int t = 0; t < RT; ++t)
-#pragma unroll
-      for (int c = 0; c < W; ++c) {
-        R v = R(0);
-        if (src >= 0 && t < nk) {
-          const long long a = (src * is_e + (long long)(k0 + t) * is_k) * W + c;
-          v = in0[a];
-          if (MODE == ADJ_ID && in1) v += in1[a];
-          v *= w;
-        }
-        xs[(t * ldx_max + j) * W + c] = v;
-      }
   }
   __syncthreads();
-
-  if (MODE == ADJ_ID && it.start == 0) {  // identity part: out[skel_j] = z_j
-    for (int e = threadIdx.x; e < d.cols * nk; e += kThreads) {
-      const int j = e / nk, t = e % nk;
-      const long long dst = idx[d.idx_off + j];
-#pragma unroll
-      for (int c = 0; c < W; ++c)
-        out[(dst * os_e + (long long)(k0 + t) * os_k) * W + c] = xs[(t * ldx_max + j) * W + c];
-    }
+  unsigned cons = 0;
+  bool ok = true;
+  for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    const MhtItem it = items[item];
+    const MhtBlockDesc d = a.desc[it.blk];
+    ok = row_item<R, C, RT, MODE>(a, it, d, sm, cons, status, [&] { prod.issue(sm); });
   }
-  if (it.count == 0) return;
-
-  if (bytes > 0 && !mbar_wait_bounded(bar, 0)) {
-    if (threadIdx.x == 0) atomicOr(status, 1u);
-    mbar_wait_bounded(bar, 0);  // let the copy land before the CTA releases shared memory
-    return;
-  }
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nvec = ldt / E;
-  for (int ii = warp; ii < it.count; ii += kWarps) {
-    const int i = it.start + ii;
-    R acc[RT][W];
-#pragma unroll
-    for (int t = 0; t < RT; ++t)
-#pragma unroll
-      for (int c = 0; c < W; ++c) acc[t][c] = R(0);
-    const R* row = tile + (long long)ii * ldt * W;
-    for (int v = lane; v < nvec; v += 32) {
-      const Vec16<R> tv = *reinterpret_cast<const Vec16<R>*>(row + v * NS);
-#pragma unroll
-      for (int t = 0; t < RT; ++t) {
-        const Vec16<R> xv = *reinterpret_cast<const Vec16<R>*>(xs + (t * ldx_max + v * E) * W);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          if (C) {
-            const R a = tv.s[2 * e], b = tv.s[2 * e + 1];
-            const R xr = xv.s[2 * e], xi = xv.s[2 * e + 1];
-            acc[t][0] += a * xr - b * xi;
-            acc[t][W - 1] += a * xi + b * xr;
-          } else {
-            acc[t][0] += tv.s[e] * xv.s[e];
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < RT; ++t)
-#pragma unroll
-      for (int c = 0; c < W; ++c) acc[t][c] = warp_sum(acc[t][c]);
-    if (lane < nk) {
-      const int t = lane;
-      R val[W];
-#pragma unroll
-      for (int tt = 0; tt < RT; ++tt)
-        if (tt == t)
-#pragma unroll
-          for (int c = 0; c < W; ++c) val[c] = acc[tt][c];
-      long long dst;
-      if (MODE == SYN_ID) {
-        const long long s = idx[d.idx_off + i];
-#pragma unroll
-        for (int c = 0; c < W; ++c) val[c] += in0[(s * is_e + (long long)(k0 + t) * is_k) * W + c];
-        dst = (long long)d.out_off + i;
-      } else if (MODE == ADJ_ID) {
-        dst = idx[d.idx_off + d.cols + i];
-      } else if (MODE == SYN_U) {
-        dst = perm[d.out_off + i];
-        if (wts) {
-          const R w = wts[dst];
-#pragma unroll
-          for (int c = 0; c < W; ++c) val[c] *= w;
-        }
-      } else {
-        dst = (long long)d.in_off + i;
-      }
-#pragma unroll
-      for (int c = 0; c < W; ++c) out[(dst * os_e + (long long)(k0 + t) * os_k) * W + c] = val[c];
-    }
-  }
+  if (threadIdx.x == 0 && !ok) row_drain(sm, cons, prod.issued);
 }
 
-// ---------------------------------------------------------------------------------------
-// Persistent fused apply: every stage of one direction in a single launch.
-//
-// Three warp roles per CTA (one CTA per SM):
-//  * producer (warp 0, lane 0): takes work items from a global queue in dependency order,
-//    hands each to the gather warps through a small item queue, and streams its rows in
-//    chunks of at most one slot into a kSlots-deep shared-memory ring with 1-D TMA bulk
-//    copies (full/empty mbarriers).  Matrix tiles do not depend on earlier stages, so the
-//    producer runs ahead of the data dependencies and keeps HBM busy.
-//  * gather warps (kGatherWarps): one item ahead of the math, wait (bounded) until the
-//    blocks the item reads are complete, then stage its input vector, its identity terms
-//    and its output indices in one of two shared-memory buffers.
-//  * compute warps (kComputeWarps): for every chunk, reduce rows from shared memory and
-//    store results; the last warp to finish an item publishes it with a release fence and a
-//    per-block completion counter.  No CTA-wide barrier sits on this path.
-// Items are dequeued in increasing order and only wait on smaller items, so the oldest
-// unfinished item can always proceed: no deadlock, whether or not all CTAs are resident.
-// Intermediate vectors are read with L2-only loads (.cg), so a stale L1 line from a
-// neighbouring block is never used.  Every wait is bounded in time and watches the status
-// word, so an error ends the launch instead of hanging it.
 constexpr int kSlots = 4;
 constexpr int kItemQ = 4;
 constexpr int kComputeWarps = 16;
@@ -621,33 +411,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(FusedParams<R> p) {
     for (int ii = cw; ii < m.z; ii += kComputeWarps) {
       const int il = m.y + ii;  // row within the item
       R acc[RT][W];
-#pragma unroll
-      for (int t = 0; t < RT; ++t)
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[t][c] = R(0);
-      const R* row = tile + (long long)ii * d.ldt * W;
-      for (int v = lane; v < nvec; v += 32) {
-        const Vec16<R> tv = *reinterpret_cast<const Vec16<R>*>(row + v * NS);
-#pragma unroll
-        for (int t = 0; t < RT; ++t) {
-          const Vec16<R> xv = *reinterpret_cast<const Vec16<R>*>(xb + (t * p.ldx + v * E) * W);
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            if (C) {
-              const R a = tv.s[2 * e], bb = tv.s[2 * e + 1];
-              const R xr = xv.s[2 * e], xi = xv.s[2 * e + 1];
-              acc[t][0] += a * xr - bb * xi;
-              acc[t][W - 1] += a * xi + bb * xr;
-            } else {
-              acc[t][0] += tv.s[e] * xv.s[e];
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < RT; ++t)
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[t][c] = warp_sum(acc[t][c]);
+      row_dot<R, C, RT>(tile + (long long)ii * d.ldt * W, xb, p.ldx, nvec, lane, acc);
       if (lane < nr && lane < RT) {
         const int t = lane;
         R val[W];
@@ -786,6 +550,7 @@ struct Ctx {
   cudaStream_t s;
   int64_t nrhs;
   std::string& err;
+  mht_apply_mode mode = MHT_APPLY_FP32;
 };
 
 int check(cudaError_t e, std::string& err, const char* what) {
@@ -803,65 +568,126 @@ unsigned* status_ptr(const Ctx& c) {
   return reinterpret_cast<unsigned*>(c.d.ws + c.P.status_offset(c.d.max_nrhs, c.F.n, c.F.m));
 }
 
-size_t stage_smem(const Packed& P, const Stage& S, int dir, int rt) {
-  const size_t tile = (S.dir[dir].max_tile_bytes + 127) / 128 * 128;
-  return 128 + tile + size_t(std::max<int64_t>(S.dir[dir].max_ld, 1)) * rt * P.elem_bytes;
+int num_sms();
+
+// Ring slot of the per-stage kernel: slot_kb KB (default 32), or one padded row if wider.
+size_t stage_slot_bytes(const Packed& P, const Stage& S, int dir, int slot_kb = 0) {
+  const size_t row = size_t(std::max<int64_t>(S.dir[dir].max_ld, 1)) * P.elem_bytes;
+  return std::max<size_t>(size_t(slot_kb > 0 ? slot_kb : 32) * 1024, (row + 127) / 128 * 128);
+}
+
+size_t stage_smem(const Packed& P, const Stage& S, int dir, int rt, int nslot, int slot_kb = 0) {
+  const size_t rows = size_t(std::max<int64_t>(S.dir[dir].max_item_rows, 1));
+  return 128 + nslot * stage_slot_bytes(P, S, dir, slot_kb) +
+         size_t(std::max<int64_t>(S.dir[dir].max_ld, 1)) * rt * P.elem_bytes + rows * rt * P.elem_bytes +
+         rows * sizeof(int);
+}
+
+// Default ring: kRowSlots slots (fewer if shared memory is short); 0 if none fits.
+int stage_nslot(const Packed& P, const Stage& S, int dir, int rt, int slot_kb = 0, int max_slots = kRowSlots) {
+  for (int ns = max_slots; ns >= 1; --ns)
+    if (stage_smem(P, S, dir, rt, ns, slot_kb) <= 227 * 1024) return ns;
+  return 0;
 }
 
 template <class R, bool C, int RT, int MODE>
 int launch(const Ctx& c, int s, const void* in0, const void* in1, long long is_e, long long is_k, void* out0,
-           void* out1, long long os_e, long long os_k, const void* w) {
+           void* out1, long long os_e, long long os_k, const void* w, const StageCfg& cfg) {
   const int dir = (MODE == ADJ_ID || MODE == ADJ_U) ? 1 : 0;
   const Stage& S = c.P.st[s];
   const StageDir& D = S.dir[dir];
   if (D.nitems == 0) return 0;
-  const size_t smem = stage_smem(c.P, S, dir, RT);
-  if (smem > 227 * 1024) {
+  const int nslot = stage_nslot(c.P, S, dir, RT, cfg.slot_kb, cfg.nslot > 0 ? cfg.nslot : kRowSlots);
+  if (nslot == 0) {
     c.err = "a stage needs more shared memory than an SM has for this RHS tile";
     return MHT_ERR_UNSUPPORTED;
   }
+  const size_t smem = stage_smem(c.P, S, dir, RT, nslot, cfg.slot_kb);
   auto kern = k_rowdot<R, C, RT, MODE>;
   if (smem > 48 * 1024)
     if (int rc = check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), c.err,
                        "shared memory attribute"))
       return rc;
   const uint8_t* base = c.d.base;
-  dim3 grid(unsigned(D.nitems), unsigned((c.nrhs + RT - 1) / RT));
+  RowArgs<R> a{reinterpret_cast<const R*>(base + c.P.data_off), reinterpret_cast<const int*>(base + c.P.index_off),
+               reinterpret_cast<const MhtBlockDesc*>(base + D.desc_off), reinterpret_cast<const int*>(base + c.P.perm_off),
+               static_cast<const R*>(w), static_cast<const R*>(in0), static_cast<const R*>(in1), is_e, is_k,
+               static_cast<R*>(out0), static_cast<R*>(out1), os_e, os_k, int(c.nrhs)};
+  int per_sm = 0;
+  if (int rc = check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem), c.err, "occupancy"))
+    return rc;
+  per_sm = std::max(per_sm, 1);
+  if (cfg.per_sm > 0) per_sm = std::min(per_sm, cfg.per_sm);
+  const int64_t grid = std::min<int64_t>(D.nitems, int64_t(per_sm) * num_sms());
   StageTimer timer(c.d.prof, dir, s, c.s);
-  kern<<<grid, kThreads, smem, c.s>>>(
-      reinterpret_cast<const R*>(base + c.P.data_off), reinterpret_cast<const int*>(base + c.P.index_off),
-      reinterpret_cast<const MhtBlockDesc*>(base + D.desc_off), reinterpret_cast<const MhtItem*>(base + D.items_off),
-      reinterpret_cast<const int*>(base + c.P.perm_off), static_cast<const R*>(w), static_cast<const R*>(in0),
-      static_cast<const R*>(in1), is_e, is_k, static_cast<R*>(out0), static_cast<R*>(out1), os_e, os_k,
-      int(c.nrhs), int(D.max_tile_bytes), int(std::max<int64_t>(D.max_ld, 1)), status_ptr(c));
+  kern<<<unsigned(grid), kThreads, smem, c.s>>>(a, reinterpret_cast<const MhtItem*>(base + D.items_off), int(D.nitems),
+                                               int(stage_slot_bytes(c.P, S, dir, cfg.slot_kb)), nslot,
+                                               int(std::max<int64_t>(D.max_ld, 1)),
+                                               int(std::max<int64_t>(D.max_item_rows, 1)), status_ptr(c));
   return check(cudaGetLastError(), c.err, "apply launch");
 }
 
 template <class R, bool C, int RT>
-int synth_impl(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool weighted) {
-  const int L = c.F.L;
-  const long long nr = c.nrhs;
-  int rc = launch<R, C, RT, SYN_ID>(c, 0, cin, nullptr, 1, ldc, lvl(c, 0, 0), nullptr, nr, 1, nullptr);
-  for (int l = 1; l <= L && !rc; ++l)
-    rc = launch<R, C, RT, SYN_ID>(c, l, lvl(c, 0, l - 1), nullptr, nr, 1, lvl(c, 0, l), nullptr, nr, 1, nullptr);
-  if (rc) return rc;
-  const void* w = weighted ? (const void*)(c.d.base + c.P.weights_off) : nullptr;
-  return launch<R, C, RT, SYN_U>(c, L + 1, lvl(c, 0, L), nullptr, nr, 1, f, nullptr, 1, ldf, w);
+int launch_mode(const Ctx& c, int s, int mode, const void* in0, const void* in1, long long is_e, long long is_k,
+                void* out0, void* out1, long long os_e, long long os_k, const void* w, const StageCfg& cfg) {
+  switch (mode) {
+    case SYN_ID: return launch<R, C, RT, SYN_ID>(c, s, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+    case ADJ_ID: return launch<R, C, RT, ADJ_ID>(c, s, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+    case SYN_U: return launch<R, C, RT, SYN_U>(c, s, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+    default: return launch<R, C, RT, ADJ_U>(c, s, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+  }
 }
 
-template <class R, bool C, int RT>
-int adjoint_impl(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t ldc, bool weighted) {
+int tc_launch(const Ctx& c, int s, int dir, int mode, const void* in0, const void* in1, long long is_e,
+              long long is_k, void* out0, void* out1, long long os_e, long long os_k, const void* w);
+
+// One stage with the given configuration: the SIMT kernel with RHS tile cfg.rt, or (FP32
+// plans) the tensor-core kernel.
+template <class R, bool C>
+int run_stage(const Ctx& c, int s, int mode, const void* in0, const void* in1, long long is_e, long long is_k,
+              void* out0, void* out1, long long os_e, long long os_k, const void* w, const StageCfg& cfg) {
+  if constexpr (sizeof(R) == 4) {
+    if (cfg.tensor) {
+      const int dir = (mode == ADJ_ID || mode == ADJ_U) ? 1 : 0;
+      return tc_launch(c, s, dir, mode, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w);
+    }
+  }
+  switch (cfg.rt) {
+    case 8: return launch_mode<R, C, 8>(c, s, mode, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+    case 4: return launch_mode<R, C, 4>(c, s, mode, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+    case 2: return launch_mode<R, C, 2>(c, s, mode, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+    default: return launch_mode<R, C, 1>(c, s, mode, in0, in1, is_e, is_k, out0, out1, os_e, os_k, w, cfg);
+  }
+}
+
+// The stages of one direction in apply order: synthesis V, R (l = 1..L), U; the adjoint U^H,
+// R^H (l = L..1), V^H.  cfg(dir, s) gives each stage's configuration.
+template <class R, bool C, class Cfg>
+int synth_stages(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool weighted, Cfg&& cfg) {
+  const int L = c.F.L;
+  const long long nr = c.nrhs;
+  int rc = run_stage<R, C>(c, 0, SYN_ID, cin, nullptr, 1, ldc, lvl(c, 0, 0), nullptr, nr, 1, nullptr, cfg(0, 0));
+  for (int l = 1; l <= L && !rc; ++l)
+    rc = run_stage<R, C>(c, l, SYN_ID, lvl(c, 0, l - 1), nullptr, nr, 1, lvl(c, 0, l), nullptr, nr, 1, nullptr,
+                         cfg(0, l));
+  if (rc) return rc;
+  const void* w = weighted ? (const void*)(c.d.base + c.P.weights_off) : nullptr;
+  return run_stage<R, C>(c, L + 1, SYN_U, lvl(c, 0, L), nullptr, nr, 1, f, nullptr, 1, ldf, w, cfg(0, L + 1));
+}
+
+template <class R, bool C, class Cfg>
+int adjoint_stages(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t ldc, bool weighted, Cfg&& cfg) {
   const int L = c.F.L;
   const long long nr = c.nrhs;
   const void* w = weighted ? (const void*)(c.d.base + c.P.weights_off) : nullptr;
   // U^H: f -> z_L (region A0, level L)
-  int rc = launch<R, C, RT, ADJ_U>(c, L + 1, f, nullptr, 1, ldf, lvl(c, 1, L), nullptr, nr, 1, w);
+  int rc = run_stage<R, C>(c, L + 1, ADJ_U, f, nullptr, 1, ldf, lvl(c, 1, L), nullptr, nr, 1, w, cfg(1, L + 1));
   for (int l = L; l >= 1 && !rc; --l)
-    rc = launch<R, C, RT, ADJ_ID>(c, l, lvl(c, 1, l), l == L ? nullptr : lvl(c, 2, l), nr, 1, lvl(c, 1, l - 1),
-                                  lvl(c, 2, l - 1), nr, 1, nullptr);
+    rc = run_stage<R, C>(c, l, ADJ_ID, lvl(c, 1, l), l == L ? nullptr : lvl(c, 2, l), nr, 1, lvl(c, 1, l - 1),
+                         lvl(c, 2, l - 1), nr, 1, nullptr, cfg(1, l));
   if (rc) return rc;
-  return launch<R, C, RT, ADJ_ID>(c, 0, lvl(c, 1, 0), L == 0 ? nullptr : lvl(c, 2, 0), nr, 1, cout, cout, 1, ldc,
-                                  nullptr);
+  return run_stage<R, C>(c, 0, ADJ_ID, lvl(c, 1, 0), L == 0 ? nullptr : lvl(c, 2, 0), nr, 1, cout, cout, 1, ldc,
+                         nullptr, cfg(1, 0));
 }
 
 int num_sms() {
@@ -938,7 +764,7 @@ int fused_launch(const Ctx& c, const void* in, long long ld_in, void* out, long 
 
 // Smallest RHS tile (1, 2, 4, 8) that covers nrhs in one fused launch, or 0 if none fits.
 int fused_rt(const Ctx& c, int dir) {
-  if (c.d.path == 1 || c.nrhs > 8) return 0;
+  if (c.d.path != 2 || c.nrhs > 8) return 0;
   for (int rt = 1; rt <= 8; rt *= 2)
     if (rt >= c.nrhs) return fused_smem(c.P, dir, rt) <= 227 * 1024 ? rt : 0;
   return 0;
@@ -954,50 +780,201 @@ int fused_dispatch(const Ctx& c, int rt, const void* in, long long ld_in, void* 
   }
 }
 
+// ---- tensor-core stages (3xTF32, FP32 plans, at least 16 real or 8 complex RHS) ----------
+bool use_tc(const Ctx& c) { return c.mode == MHT_APPLY_3XTF32 && !c.P.fp64 && c.nrhs >= (c.P.cplx ? 8 : 16); }
+
+int tc_launch(const Ctx& c, int s, int dir, int mode, const void* in0, const void* in1, long long is_e,
+              long long is_k, void* out0, void* out1, long long os_e, long long os_k, const void* w) {
+  const StageDir& D = c.P.st[s].dir[dir];
+  TcLaunch a;
+  a.data = reinterpret_cast<const float*>(c.d.base + c.P.data_off);
+  a.idx = reinterpret_cast<const int*>(c.d.base + c.P.index_off);
+  a.desc = reinterpret_cast<const MhtBlockDesc*>(c.d.base + D.desc_off);
+  a.items = reinterpret_cast<const MhtItem*>(c.d.base + D.tc_items_off);
+  a.nitems = D.tc_nitems;
+  a.perm = reinterpret_cast<const int*>(c.d.base + c.P.perm_off);
+  a.wts = static_cast<const float*>(w);
+  a.in0 = static_cast<const float*>(in0);
+  a.in1 = static_cast<const float*>(in1);
+  a.is_e = is_e;
+  a.is_k = is_k;
+  a.out0 = static_cast<float*>(out0);
+  a.out1 = static_cast<float*>(out1);
+  a.os_e = os_e;
+  a.os_k = os_k;
+  a.nrhs = c.nrhs;
+  a.mode = mode;
+  a.cplx = c.P.cplx ? 1 : 0;
+  a.status = status_ptr(c);
+  a.stream = c.s;
+  StageTimer timer(c.d.prof, dir, s, c.s);
+  return tc_stage_launch(a, c.err);
+}
+
 // Largest RHS tile (8, 4, 2, 1), at most nrhs, whose shared memory fits every stage.
 int pick_rt(const Ctx& c, int dir) {
   for (int rt = 8; rt >= 1; rt /= 2) {
     if (rt > 1 && c.nrhs < rt) continue;
     bool ok = true;
-    for (const Stage& s : c.P.st) ok = ok && stage_smem(c.P, s, dir, rt) <= 227 * 1024;
+    for (const Stage& s : c.P.st) ok = ok && stage_nslot(c.P, s, dir, rt) > 0;
     if (ok) return rt;
   }
   return 1;
 }
 
+// Configuration of stage s in direction dir for this apply: the autotuned one when the plan
+// was tuned for this RHS count, else the defaults (tensor cores in 3xTF32 mode from 16 real /
+// 8 complex RHS, else the widest RHS tile that fits, all ring slots, all resident CTAs).
+StageCfg stage_cfg(const Ctx& c, int dir, int s, int default_rt) {
+  if (c.d.tune_nrhs == c.nrhs && size_t(s) < c.d.tune[dir].size() &&
+      (c.d.tune_mode == c.mode || !c.d.tune[dir][s].tensor))
+    return c.d.tune[dir][s];
+  StageCfg g;
+  g.tensor = use_tc(c) ? 1 : 0;
+  g.rt = default_rt;
+  return g;
+}
+
 template <class R, bool C>
 int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool wt) {
-  if (const int rt = fused_rt(c, 0)) {
-    const int rc = fused_dispatch<R, C, 0>(c, rt, cin, ldc, f, ldf, wt);
-    if (rc >= 0) return rc;
-  }
+  if (!use_tc(c) && (c.d.path == 2 || c.d.tune_nrhs != c.nrhs))
+    if (const int rt = fused_rt(c, 0)) {
+      const int rc = fused_dispatch<R, C, 0>(c, rt, cin, ldc, f, ldf, wt);
+      if (rc >= 0) return rc;
+    }
   if (c.d.path == 2) {
     c.err = "the fused apply does not fit this plan / RHS count";
     return MHT_ERR_UNSUPPORTED;
   }
-  switch (pick_rt(c, 0)) {
-    case 8: return synth_impl<R, C, 8>(c, cin, ldc, f, ldf, wt);
-    case 4: return synth_impl<R, C, 4>(c, cin, ldc, f, ldf, wt);
-    case 2: return synth_impl<R, C, 2>(c, cin, ldc, f, ldf, wt);
-    default: return synth_impl<R, C, 1>(c, cin, ldc, f, ldf, wt);
-  }
+  const int rt = pick_rt(c, 0);
+  return synth_stages<R, C>(c, cin, ldc, f, ldf, wt, [&](int dir, int s) { return stage_cfg(c, dir, s, rt); });
 }
 template <class R, bool C>
 int adjoint_dispatch(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t ldc, bool wt) {
-  if (const int rt = fused_rt(c, 1)) {
-    const int rc = fused_dispatch<R, C, 1>(c, rt, f, ldf, cout, ldc, wt);
-    if (rc >= 0) return rc;
-  }
+  if (!use_tc(c) && (c.d.path == 2 || c.d.tune_nrhs != c.nrhs))
+    if (const int rt = fused_rt(c, 1)) {
+      const int rc = fused_dispatch<R, C, 1>(c, rt, f, ldf, cout, ldc, wt);
+      if (rc >= 0) return rc;
+    }
   if (c.d.path == 2) {
     c.err = "the fused apply does not fit this plan / RHS count";
     return MHT_ERR_UNSUPPORTED;
   }
-  switch (pick_rt(c, 1)) {
-    case 8: return adjoint_impl<R, C, 8>(c, f, ldf, cout, ldc, wt);
-    case 4: return adjoint_impl<R, C, 4>(c, f, ldf, cout, ldc, wt);
-    case 2: return adjoint_impl<R, C, 2>(c, f, ldf, cout, ldc, wt);
-    default: return adjoint_impl<R, C, 1>(c, f, ldf, cout, ldc, wt);
+  const int rt = pick_rt(c, 1);
+  return adjoint_stages<R, C>(c, f, ldf, cout, ldc, wt, [&](int dir, int s) { return stage_cfg(c, dir, s, rt); });
+}
+
+// ---- autotuner ---------------------------------------------------------------------------
+// Times every candidate configuration of every stage (RHS tile, ring slots, resident CTAs per
+// SM, tensor cores or not) on the bound workspace and keeps the fastest.  Each stage runs on
+// its own (zeroed) buffers: stage 0 reads the host-staging area for c, the last stage writes
+// the one for f, so nothing of the caller's is touched.
+template <class R, bool C>
+int autotune(Ctx& c, DeviceView& dv, std::vector<TuneRecord>* report) {
+  const Packed& P = c.P;
+  const int L = c.F.L;
+  const int64_t nr = c.nrhs;
+  // host-staging areas of the workspace: c (m x max_nrhs) then f (n x max_nrhs)
+  uint8_t* cbuf = dv.ws + 3 * P.ws_vec_bytes(dv.max_nrhs);
+  uint8_t* fbuf = dv.ws + P.ws_counters_offset(dv.max_nrhs, c.F.n, c.F.m) -
+                  (size_t(c.F.n) * dv.max_nrhs * P.elem_bytes + 255) / 256 * 256;
+  if (int rc = check(cudaMemsetAsync(dv.ws, 0, P.ws_counters_offset(dv.max_nrhs, c.F.n, c.F.m), c.s), c.err, "tune zero"))
+    return rc;
+  std::vector<StageCfg> cands;
+  const bool tc_ok = sizeof(R) == 4 && c.mode == MHT_APPLY_3XTF32;
+  // single RHS (bandwidth-bound): the ring's slot size and depth and the resident CTAs;
+  // several RHS (issue-bound): the RHS tile, a few ring depths and CTA counts
+  auto add = [&](int rt, int kb, int ns, int ps) {
+    StageCfg g;
+    g.rt = rt;
+    g.slot_kb = kb;
+    g.nslot = ns;
+    g.per_sm = ps;
+    cands.push_back(g);
+  };
+  if (nr == 1) {
+    for (int kb : {16, 32, 64})
+      for (int ns = 1; ns <= kMaxRowSlots && ns * kb <= 192; ++ns)
+        for (int ps = 1; ps <= 4; ++ps) add(1, kb, ns, ps);
+  } else {
+    for (int rt : {2, 4, 8})
+      if (rt <= nr && (rt == 8 || 2 * rt > nr))  // the widest tile that fits, and 8
+        for (int ns = 1; ns <= kRowSlots; ++ns)
+          for (int ps = 1; ps <= 2; ++ps) add(rt, 32, ns, ps);
   }
+  if (tc_ok) {
+    StageCfg g;
+    g.tensor = 1;
+    cands.push_back(g);
+  }
+  cudaEvent_t e0, e1;
+  if (int rc = check(cudaEventCreate(&e0), c.err, "event")) return rc;
+  if (int rc = check(cudaEventCreate(&e1), c.err, "event")) return rc;
+  int rc = 0;
+  for (int dir = 0; dir < 2 && !rc; ++dir) {
+    dv.tune[dir].assign(L + 2, StageCfg());
+    for (int s = 0; s < L + 2 && !rc; ++s) {
+      if (P.st[s].dir[dir].nitems == 0) continue;
+      float best = 1e30f;
+      StageCfg best_cfg;
+      for (const StageCfg& g : cands) {
+        // skip slot / CTA counts that do not fit: they would repeat a smaller configuration
+        if (!g.tensor) {
+          const int fit = stage_nslot(P, P.st[s], dir, g.rt, g.slot_kb, kMaxRowSlots);
+          if (g.nslot > fit) continue;
+          if (stage_slot_bytes(P, P.st[s], dir, g.slot_kb) > size_t(g.slot_kb) * 1024 && g.slot_kb != 64) continue;
+          const size_t smem = stage_smem(P, P.st[s], dir, g.rt, g.nslot, g.slot_kb);
+          if (g.per_sm > 1 && size_t(g.per_sm) * (smem + 1024) > 228 * 1024) continue;  // cannot be resident
+        }
+        // the stage's own input and output levels, each in its own region (exact sizes)
+        auto one = [&]() -> int {
+          if (dir == 0) {
+            const void* in0 = s == 0 ? (const void*)cbuf : lvl(c, 0, s - 1);
+            void* out0 = s == L + 1 ? (void*)fbuf : lvl(c, 1, s);
+            return run_stage<R, C>(c, s, s == L + 1 ? SYN_U : SYN_ID, in0, nullptr, s == 0 ? 1 : nr,
+                                   s == 0 ? c.F.m : 1, out0, nullptr, s == L + 1 ? 1 : nr, s == L + 1 ? c.F.n : 1,
+                                   nullptr, g);
+          }
+          if (s == L + 1)
+            return run_stage<R, C>(c, s, ADJ_U, fbuf, nullptr, 1, c.F.n, lvl(c, 2, L), nullptr, nr, 1, nullptr, g);
+          void* out0 = s == 0 ? (void*)cbuf : lvl(c, 2, s - 1);
+          return run_stage<R, C>(c, s, ADJ_ID, lvl(c, 1, s), nullptr, nr, 1, out0, out0, s == 0 ? 1 : nr,
+                                 s == 0 ? c.F.m : 1, nullptr, g);
+        };
+        if ((rc = one())) {  // a configuration that cannot launch is skipped
+          rc = 0;
+          cudaGetLastError();
+          continue;
+        }
+        float ms = 0.f;
+        constexpr int kReps = 3;
+        if ((rc = check(cudaEventRecord(e0, c.s), c.err, "event"))) break;
+        for (int r = 0; r < kReps && !rc; ++r) rc = one();
+        if (rc) break;
+        if ((rc = check(cudaEventRecord(e1, c.s), c.err, "event"))) break;
+        if ((rc = check(cudaEventSynchronize(e1), c.err, "event sync"))) break;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= kReps;
+        if (ms < best) {
+          best = ms;
+          best_cfg = g;
+        }
+      }
+      dv.tune[dir][s] = best_cfg;
+      if (report) report->push_back({dir, s, best_cfg, double(best)});
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    dv.tune[0].clear();
+    dv.tune[1].clear();
+    dv.tune_nrhs = 0;
+    return rc;
+  }
+  dv.tune_nrhs = nr;
+  dv.tune_mode = c.mode;
+  return check(cudaStreamSynchronize(c.s), c.err, "tune sync");
 }
 
 }  // namespace
@@ -1005,18 +982,24 @@ int adjoint_dispatch(const Ctx& c, const void* f, int64_t ldf, void* cout, int64
 int apply_synthesize(const Factorization& F, const Packed& P, const DeviceView& d, const void* c, int64_t ldc,
                      void* f, int64_t ldf, int64_t nrhs, bool wt, mht_apply_mode mode, void* stream,
                      std::string& err) {
-  Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err};
-  (void)mode;
+  Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err, mode};
   if (P.fp64)
     return P.cplx ? synth_dispatch<double, true>(x, c, ldc, f, ldf, wt)
                   : synth_dispatch<double, false>(x, c, ldc, f, ldf, wt);
   return P.cplx ? synth_dispatch<float, true>(x, c, ldc, f, ldf, wt) : synth_dispatch<float, false>(x, c, ldc, f, ldf, wt);
 }
 
+int apply_autotune(const Factorization& F, const Packed& P, DeviceView& d, int64_t nrhs, mht_apply_mode mode,
+                   void* stream, std::vector<TuneRecord>* report, std::string& err) {
+  d.tune_nrhs = 0;  // tune with the default configurations out of the way
+  Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err, mode};
+  if (P.fp64) return P.cplx ? autotune<double, true>(x, d, report) : autotune<double, false>(x, d, report);
+  return P.cplx ? autotune<float, true>(x, d, report) : autotune<float, false>(x, d, report);
+}
+
 int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, const void* f, int64_t ldf, void* c,
                   int64_t ldc, int64_t nrhs, bool weighted, mht_apply_mode mode, void* stream, std::string& err) {
-  Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err};
-  (void)mode;
+  Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err, mode};
   if (P.fp64)
     return P.cplx ? adjoint_dispatch<double, true>(x, f, ldf, c, ldc, weighted)
                   : adjoint_dispatch<double, false>(x, f, ldf, c, ldc, weighted);
@@ -1026,7 +1009,7 @@ int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, 
 
 int64_t apply_launches(const Packed& P, int64_t nrhs, mht_apply_mode mode, int path) {
   (void)mode;
-  if (path != 1 && nrhs <= 8) {
+  if (path == 2 && nrhs <= 8) {
     int rt = 1;
     while (rt < nrhs) rt *= 2;
     if (fused_smem(P, 0, rt) <= 227 * 1024) return P.fused[0].nitems > 0 ? 1 : 0;

@@ -125,6 +125,22 @@ mht_status mht_plan_import(const mht_factors* factors, const mht_options* option
   });
 }
 
+mht_status mht_plan_clone(const mht_plan* src, const mht_options* options, mht_plan** out) {
+  return guarded([&]() -> mht_status {
+    if (!src || !options || !out) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    check_mode(options->mode);
+    std::unique_ptr<mht_plan> plan(new mht_plan());
+    plan->F = src->F;
+    plan->mode = options->mode;
+    plan->eps = src->eps;
+    plan->build_seconds = src->build_seconds;
+    mht::pack(plan->F, fp64_mode(options->mode), plan->P);
+    *out = plan.release();
+    return MHT_OK;
+  });
+}
+
 mht_status mht_plan_export(const mht_plan* plan, mht_factors* fa) {
   return guarded([&]() -> mht_status {
     if (!plan || !fa) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
@@ -369,6 +385,47 @@ mht_status mht_plan_set_path(mht_plan* plan, int32_t path) {
   });
 }
 
+mht_status mht_plan_set_mode(mht_plan* plan, mht_apply_mode mode) {
+  return guarded([&]() -> mht_status {
+    if (!plan) mht::fail(MHT_ERR_INVALID_ARG, "NULL plan");
+    if (plan->P.fp64 || (mode != MHT_APPLY_FP32 && mode != MHT_APPLY_3XTF32))
+      mht::fail(MHT_ERR_INVALID_ARG, "set_mode switches only between FP32 and 3XTF32 on a float plan");
+    plan->mode = mode;
+    return MHT_OK;
+  });
+}
+
+mht_status mht_plan_autotune(mht_plan* plan, int64_t nrhs, void* stream) {
+  return guarded([&]() -> mht_status {
+    if (!plan) mht::fail(MHT_ERR_INVALID_ARG, "NULL plan");
+    if (!plan->bound) mht::fail(MHT_ERR_NOT_BOUND, "plan is not bound to device memory");
+    if (nrhs < 1 || nrhs > plan->dev.max_nrhs) mht::fail(MHT_ERR_INVALID_ARG, "nrhs outside 1..max_nrhs");
+    std::string err;
+    plan->tune_report.clear();
+    if (int rc = mht::apply_autotune(plan->F, plan->P, plan->dev, nrhs, plan->mode, stream, &plan->tune_report, err))
+      mht::fail(mht_status(rc), err);
+    return MHT_OK;
+  });
+}
+
+mht_status mht_plan_tune_info(const mht_plan* plan, int32_t direction, int32_t stage, int32_t* cfg, double* ms) {
+  return guarded([&]() -> mht_status {
+    if (!plan || !cfg) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    for (const mht::TuneRecord& r : plan->tune_report)
+      if (r.dir == direction && r.stage == stage) {
+        cfg[0] = r.cfg.tensor;
+        cfg[1] = r.cfg.rt;
+        cfg[2] = r.cfg.nslot;
+        cfg[3] = r.cfg.per_sm;
+        cfg[4] = r.cfg.slot_kb;
+        if (ms) *ms = r.ms;
+        return MHT_OK;
+      }
+    mht::fail(MHT_ERR_INVALID_ARG, "no tuned configuration for this stage");
+    return MHT_OK;
+  });
+}
+
 mht_status mht_plan_profile(mht_plan* plan, int32_t enable) {
   return guarded([&]() -> mht_status {
     if (!plan) mht::fail(MHT_ERR_INVALID_ARG, "NULL plan");
@@ -474,3 +531,172 @@ mht_status mht_destroy(mht_plan* plan) {
 }
 
 }  // extern "C"
+
+// ---- batched apply ---------------------------------------------------------------------
+
+mht_status mht_batch_create(mht_plan* const* plans, int32_t count, const int64_t* nrhs, mht_batch** out) {
+  return guarded([&]() -> mht_status {
+    if (!out) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    std::unique_ptr<mht_batch> b(new mht_batch());
+    mht::batch_init(*b, plans, count, nrhs);
+    *out = b.release();
+    return MHT_OK;
+  });
+}
+
+mht_status mht_batch_device_bytes(const mht_batch* batch, size_t* image_bytes, size_t* workspace_bytes) {
+  return guarded([&]() -> mht_status {
+    if (!batch || !image_bytes || !workspace_bytes) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    *image_bytes = batch->image_bytes;
+    *workspace_bytes = batch->ws_bytes;
+    return MHT_OK;
+  });
+}
+
+mht_status mht_batch_bind_device(mht_batch* batch, void* image_dev, size_t image_bytes, void* workspace_dev,
+                                 size_t workspace_bytes, void* stream) {
+  return guarded([&]() -> mht_status {
+    if (!batch || !image_dev || !workspace_dev) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    if (image_bytes < batch->image_bytes || workspace_bytes < batch->ws_bytes)
+      mht::fail(MHT_ERR_INVALID_ARG, "device buffers smaller than mht_batch_device_bytes");
+    if ((reinterpret_cast<uintptr_t>(image_dev) | reinterpret_cast<uintptr_t>(workspace_dev)) & 255)
+      mht::fail(MHT_ERR_INVALID_ARG, "device buffers must be 256-byte aligned");
+    for (auto*& g : batch->graphs) {
+      mht::batch_graph_destroy(g);
+      g = nullptr;
+    }
+    batch->image_dev = static_cast<uint8_t*>(image_dev);
+    batch->ws_dev = static_cast<uint8_t*>(workspace_dev);
+    std::string err;
+    for (const mht::BatchInst& I : batch->inst)
+      if (int rc = mht::device_upload(batch->image_dev + I.image_off, I.plan->P.image.data(), I.image_bytes, stream, err))
+        mht::fail(mht_status(rc), err);
+    for (int dir = 0; dir < 2; ++dir)
+      if (int rc = mht::device_upload(batch->image_dev + batch->items_off[dir], batch->items[dir].data(),
+                                      batch->items[dir].size() * sizeof(MhtBItem), stream, err))
+        mht::fail(mht_status(rc), err);
+    std::vector<uint8_t> zero(256, 0);
+    if (int rc = mht::device_upload(batch->ws_dev + batch->status_off, zero.data(), 256, stream, err))
+      mht::fail(mht_status(rc), err);
+    for (mht::BatchInst& I : batch->inst) I.plan = nullptr;
+    batch->bound = true;
+    batch->io_set = false;
+    return MHT_OK;
+  });
+}
+
+mht_status mht_batch_set_io(mht_batch* batch, void* const* c_dev, const int64_t* ldc, void* const* f_dev,
+                            const int64_t* ldf, void* stream) {
+  return guarded([&]() -> mht_status {
+    if (!batch || !c_dev || !ldc || !f_dev || !ldf) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    if (!batch->bound) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound to device memory");
+    for (int i = 0; i < batch->n; ++i) {
+      mht::BatchInst& I = batch->inst[i];
+      if (!c_dev[i] || !f_dev[i]) mht::fail(MHT_ERR_INVALID_ARG, "NULL vector in batch");
+      if ((I.nrhs > 1 && (ldc[i] < I.m || ldf[i] < I.n)) || ldc[i] < 1 || ldf[i] < 1)
+        mht::fail(MHT_ERR_INVALID_ARG, "leading dimension smaller than the vector length");
+      I.c = reinterpret_cast<uint64_t>(c_dev[i]);
+      I.f = reinterpret_cast<uint64_t>(f_dev[i]);
+      I.ldc = ldc[i];
+      I.ldf = ldf[i];
+    }
+    mht::batch_fill_records(*batch);
+    std::string err;
+    for (int dir = 0; dir < 2; ++dir)
+      if (int rc = mht::device_upload(batch->image_dev + batch->recs_off[dir], batch->recs[dir].data(),
+                                      batch->recs[dir].size() * sizeof(MhtBatchRec), stream, err))
+        mht::fail(mht_status(rc), err);
+    batch->io_set = true;
+    return MHT_OK;
+  });
+}
+
+namespace {
+mht_status batch_run(mht_batch* batch, int dir, bool weighted, void* stream) {
+  if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
+  if (!batch->bound || !batch->io_set) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound or has no vectors");
+  std::string err;
+  const mht::BatchLaunch b = mht::batch_launch_desc(*batch, dir, weighted);
+  if (!batch->use_graph) {
+    if (int rc = mht::batch_launch(b, stream, err)) mht::fail(mht_status(rc), err);
+    return MHT_OK;
+  }
+  mht::BatchGraph*& g = batch->graphs[dir == 0 ? 0 : (weighted ? 2 : 1)];
+  if (!g)
+    if (int rc = mht::batch_graph_create(b, &g, err)) mht::fail(mht_status(rc), err);
+  if (int rc = mht::batch_graph_launch(g, stream, err)) mht::fail(mht_status(rc), err);
+  return MHT_OK;
+}
+}  // namespace
+
+mht_status mht_batch_synthesize(mht_batch* batch, void* stream) {
+  return guarded([&]() -> mht_status { return batch_run(batch, 0, false, stream); });
+}
+
+mht_status mht_batch_analyze(mht_batch* batch, int32_t weighted, void* stream) {
+  return guarded([&]() -> mht_status { return batch_run(batch, 1, weighted != 0, stream); });
+}
+
+mht_status mht_batch_set_graph(mht_batch* batch, int32_t use_graph) {
+  return guarded([&]() -> mht_status {
+    if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
+    batch->use_graph = use_graph ? 1 : 0;
+    return MHT_OK;
+  });
+}
+
+mht_status mht_batch_info(const mht_batch* batch, int64_t* items_synthesis, int64_t* items_analysis, int32_t* grid) {
+  return guarded([&]() -> mht_status {
+    if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
+    if (items_synthesis) *items_synthesis = int64_t(batch->items[0].size());
+    if (items_analysis) *items_analysis = int64_t(batch->items[1].size());
+    if (grid) {
+      std::string err;
+      const int g = mht::batch_grid_size(mht::batch_launch_desc(*batch, 0, false), err);
+      if (g < 0) mht::fail(mht_status(-g), err);
+      *grid = g;
+    }
+    return MHT_OK;
+  });
+}
+
+mht_status mht_batch_check(mht_batch* batch, void* stream, int32_t* flags) {
+  return guarded([&]() -> mht_status {
+    if (!batch || !flags) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    if (!batch->bound) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound to device memory");
+    unsigned v = 0;
+    std::string err;
+    if (int rc = mht::device_status(batch->ws_dev + batch->status_off, stream, &v, err)) mht::fail(mht_status(rc), err);
+    *flags = int32_t(v);
+    if (v) return set_error(MHT_ERR_TIMEOUT, "a bounded wait in the batched apply gave up");
+    return MHT_OK;
+  });
+}
+
+mht_status mht_batch_autotune(mht_batch* batch, void* stream, double* best_ms) {
+  return guarded([&]() -> mht_status {
+    if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
+    if (!batch->bound || !batch->io_set) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound or has no vectors");
+    batch->tuned_nslot = batch->tuned_per_sm = 0;
+    const mht::BatchLaunch syn = mht::batch_launch_desc(*batch, 0, false);
+    const mht::BatchLaunch ana = mht::batch_launch_desc(*batch, 1, true);
+    int ns = 0, ps = 0;
+    double ms = 0;
+    std::string err;
+    if (int rc = mht::batch_autotune(syn, ana, batch->nslot, stream, &ns, &ps, &ms, err)) mht::fail(mht_status(rc), err);
+    batch->tuned_nslot = ns;
+    batch->tuned_per_sm = ps;
+    for (auto*& g : batch->graphs) {  // rebuilt with the tuned shape at the next launch
+      mht::batch_graph_destroy(g);
+      g = nullptr;
+    }
+    if (best_ms) *best_ms = ms;
+    return MHT_OK;
+  });
+}
+
+mht_status mht_batch_destroy(mht_batch* batch) {
+  delete batch;
+  return MHT_OK;
+}

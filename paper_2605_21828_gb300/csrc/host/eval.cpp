@@ -87,8 +87,20 @@ struct SphereEval : Evaluator {
       lon[i] = std::atan2(y, x);
     }
   }
+  // Rows are processed in chunks so the recurrence arrays stay in L1.
   void eval(const int64_t* rows, int64_t nr, const int64_t* cols, int64_t nc,
             double* out) const override {
+    constexpr int64_t kChunk = 256;
+    if (nr <= kChunk) {
+      eval_chunk(rows, nr, cols, nc, out, nr);
+      return;
+    }
+    for (int64_t r0 = 0; r0 < nr; r0 += kChunk)
+      eval_chunk(rows + r0, std::min(kChunk, nr - r0), cols, nc, out + r0, nr);
+  }
+  // out(i, j) at out[j * ld + i]
+  void eval_chunk(const int64_t* rows, int64_t nr, const int64_t* cols, int64_t nc, double* out,
+                  int64_t ld) const {
     if (nr == 0 || nc == 0) return;
     // group requested columns by order |mm|: (l, signed mm, output column)
     std::map<int64_t, std::vector<std::array<int64_t, 3>>> groups;
@@ -128,7 +140,7 @@ struct SphereEval : Evaluator {
       auto emit = [&](int64_t l, const std::vector<double>& P) {
         while (next < list.size() && list[next][0] == l) {
           const int64_t mm = list[next][1];
-          double* o = out + list[next][2] * nr;
+          double* o = out + list[next][2] * ld;
           if (mm == 0)
             for (int64_t i = 0; i < nr; ++i) o[i] = P[i];
           else if (mm > 0)

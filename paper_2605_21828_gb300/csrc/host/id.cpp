@@ -331,9 +331,53 @@ int qrcp_id_blocked(double* A, int64_t M, int64_t K, double eps, uint64_t seed, 
 
 }  // namespace
 
+// Full-rank certificate for very tall blocks (M >= 16K): the Gram matrix A^T A by one GEMM and a
+// diagonally pivoted Cholesky factorization.  Its pivots are the squared diagonal of the
+// column-pivoted R, so if every pivot exceeds (10 eps)^2 times the largest column norm
+// squared, QRCP would keep all K columns and the ID is the identity (rank K, empty T~).
+// The factor 10 keeps the decision far above the rounding of the Gram matrix (~1e-16);
+// blocks that do not pass go to the QR.
+bool certify_full_rank(const double* A, int64_t M, int64_t K, double eps) {
+  std::vector<double> G(size_t(K) * K);
+  gemm(true, int(K), int(K), int(M), 1.0, A, int(M), A, int(M), 0.0, G.data(), int(K));
+  double dmax = 0;
+  for (int64_t j = 0; j < K; ++j) dmax = std::max(dmax, G[j * K + j]);
+  if (!(dmax > 0) || !std::isfinite(dmax)) return false;
+  const double floor = 100.0 * eps * eps * dmax;
+  std::vector<int64_t> piv(K);
+  std::iota(piv.begin(), piv.end(), int64_t(0));
+  std::vector<double> d(K);
+  for (int64_t j = 0; j < K; ++j) d[j] = G[j * K + j];
+  // right-looking pivoted Cholesky on the permuted Gram matrix (lower triangle, in place)
+  std::vector<double> Lc(size_t(K) * K, 0.0);
+  for (int64_t k = 0; k < K; ++k) {
+    int64_t p = k;
+    for (int64_t j = k + 1; j < K; ++j)
+      if (d[piv[j]] > d[piv[p]]) p = j;
+    std::swap(piv[k], piv[p]);
+    const double pk = d[piv[k]];
+    if (!(pk > floor)) return false;
+    const double lkk = std::sqrt(pk);
+    for (int64_t j = k + 1; j < K; ++j) {
+      double v = G[piv[j] * K + piv[k]];
+      for (int64_t q = 0; q < k; ++q) v -= Lc[q * K + piv[j]] * Lc[q * K + piv[k]];
+      v /= lkk;
+      Lc[k * K + piv[j]] = v;
+      d[piv[j]] -= v * v;
+    }
+  }
+  return true;
+}
+
 int interpolative_decomposition_real(double* A, int64_t M, int64_t K, double eps,
                                      std::vector<int32_t>& perm, std::vector<double>& T, uint64_t seed,
                                      bool blocked) {
+  if (blocked && K >= 32 && M >= 16 * K && certify_full_rank(A, M, K, eps)) {
+    perm.resize(K);
+    std::iota(perm.begin(), perm.end(), 0);
+    T.clear();
+    return int(K);
+  }
   if (blocked && std::min(M, K) >= 128) return qrcp_id_blocked(A, M, K, eps, seed, perm, T);
   return qrcp_id<double>(A, M, K, eps, perm, T);
 }

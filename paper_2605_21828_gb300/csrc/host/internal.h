@@ -89,7 +89,10 @@ struct StageDir {
   int64_t nitems = 0;
   int64_t max_ld = 0;                  // widest padded row (elements)
   size_t max_tile_bytes = 0;           // largest work-item matrix tile
+  int64_t max_item_rows = 0;           // most rows in one work item
   size_t data_bytes = 0;               // padded device bytes of this direction's matrices
+  size_t tc_items_off = 0;             // 128-row tiles for the tensor-core stages
+  int64_t tc_nitems = 0;
 };
 
 struct Stage {
@@ -138,6 +141,19 @@ void pack(const Factorization& F, bool fp64, Packed& P);
 // Device binding and apply (implemented in the CUDA translation unit).
 namespace mht {
 struct Profiler;  // per-stage CUDA event records (apply.cu)
+// Launch configuration of one stage (0 = default / all that fit).
+struct StageCfg {
+  int tensor = 0;  // 3xTF32 tensor-core kernel instead of the SIMT one
+  int rt = 1;      // SIMT RHS tile
+  int nslot = 0;   // bulk-copy ring slots
+  int slot_kb = 0; // ring slot size in KB (0: 32)
+  int per_sm = 0;  // resident CTAs per SM
+};
+struct TuneRecord {
+  int dir, stage;
+  StageCfg cfg;
+  double ms;
+};
 struct DeviceView {
   const uint8_t* base = nullptr;  // bound factor image
   uint8_t* ws = nullptr;          // workspace
@@ -145,6 +161,9 @@ struct DeviceView {
   int64_t max_nrhs = 0;
   Profiler* prof = nullptr;       // non-null while stage timing is enabled
   int path = 0;                   // 0 auto, 1 per-stage launches, 2 fused persistent launch
+  int64_t tune_nrhs = 0;          // RHS count the stage configurations were tuned for (0: none)
+  mht_apply_mode tune_mode = MHT_APPLY_FP32;
+  std::vector<StageCfg> tune[2];  // per direction and stage
 };
 Profiler* profiler_create();
 void profiler_destroy(Profiler* p);
@@ -156,15 +175,66 @@ int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, 
                   int64_t ldf, void* c, int64_t ldc, int64_t nrhs, bool weighted,
                   mht_apply_mode mode, void* stream, std::string& err);
 int64_t apply_launches(const Packed& P, int64_t nrhs, mht_apply_mode mode, int path);
+// Times the candidate configurations of every stage for `nrhs` RHS and stores the fastest in
+// d.tune (used by later applies with that RHS count); synchronizes `stream`.
+int apply_autotune(const Factorization& F, const Packed& P, DeviceView& d, int64_t nrhs, mht_apply_mode mode,
+                   void* stream, std::vector<TuneRecord>* report, std::string& err);
 int device_upload(void* dst, const void* src, size_t bytes, void* stream, std::string& err);
 int device_copy_async(void* dst, const void* src, size_t bytes, int kind, void* stream,
                       std::string& err);
 int device_sync(void* stream, std::string& err);
+// One stage of a multi-RHS apply on the tensor cores (3xTF32, FP32 plans, real or complex).
+struct TcLaunch {
+  const float* data;
+  const int* idx;
+  const MhtBlockDesc* desc;
+  const MhtItem* items;
+  int64_t nitems;
+  const int* perm;
+  const float* wts;
+  const float* in0;
+  const float* in1;
+  long long is_e, is_k;
+  float* out0;
+  float* out1;
+  long long os_e, os_k;
+  int64_t nrhs;
+  int mode;  // 0 synthesis ID stage, 1 adjoint ID stage, 2 synthesis column bases, 3 adjoint
+  int cplx;  // complex factors and vectors (interleaved float pairs)
+  unsigned* status;
+  void* stream;
+};
+int tc_stage_launch(const TcLaunch& a, std::string& err);
 // Fused FP32 synthesis of one vector with scratch from a fixed library array (no allocation).
 int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void* c, void* f, void* stream,
                              std::string& err);
 // Copies the device status word to *flags, clears it, and synchronizes the stream.
 int device_status(void* status_dev, void* stream, unsigned* flags, std::string& err);
+
+// Batched apply of many FP32 plans in one persistent launch (batch.cu).
+struct BatchLaunch {
+  const void* recs;         // MhtBatchRec[] of the direction (device)
+  const void* items;        // MhtBItem[] of the direction, dependency order (device)
+  int nitems;
+  unsigned* ticket;         // queue head, abort word and completion counters: all inside
+  unsigned* abort;          // [counters, counters + counter_bytes), zeroed before every launch
+  unsigned* done;
+  void* counters;
+  size_t counter_bytes;
+  unsigned* status;         // status word (bit 0 copy wait, bit 1 dependency wait gave up)
+  int use_wts;
+  int slot_bytes, nslot, ldx_max, rows_max;  // shared-memory layout maxima over all items
+  int per_sm;               // resident CTAs per SM (0: as many as fit)
+};
+struct BatchGraph;
+size_t batch_smem(int slot_bytes, int nslot, int ldx_max, int rows_max);
+int batch_launch(const BatchLaunch& b, void* stream, std::string& err);
+int batch_graph_create(const BatchLaunch& b, BatchGraph** g, std::string& err);
+int batch_graph_launch(BatchGraph* g, void* stream, std::string& err);
+void batch_graph_destroy(BatchGraph* g);
+int batch_grid_size(const BatchLaunch& b, std::string& err);  // CTAs of one launch (< 0: error)
+int batch_autotune(const BatchLaunch& syn, const BatchLaunch& ana, int max_nslot, void* stream, int* nslot,
+                   int* per_sm, double* best_ms, std::string& err);
 }  // namespace mht
 
 struct mht_plan {
@@ -174,6 +244,48 @@ struct mht_plan {
   double eps = 0;
   double build_seconds = 0;
   mht::DeviceView dev;
+  std::vector<mht::TuneRecord> tune_report;
   bool bound = false;
   ~mht_plan() { mht::profiler_destroy(dev.prof); }
 };
+
+// A batch of FP32 plans applied together (batch.cpp, batch.cu).
+namespace mht {
+struct BatchInst {
+  const mht_plan* plan = nullptr;  // needed until the batch is bound
+  int64_t n = 0, m = 0, nrhs = 1;
+  int L = 0, es = 4;
+  bool cplx = false;
+  std::vector<int64_t> vec_off;
+  size_t image_off = 0, image_bytes = 0, data_off = 0, index_off = 0, perm_off = 0, weights_off = 0;
+  std::vector<size_t> desc_off[2];  // per stage, relative to the instance image
+  int rec_base[2] = {0, 0}, ctr_base[2] = {0, 0};
+  size_t ws_off = 0, region_bytes = 0;
+  uint64_t c = 0, f = 0;            // caller vectors (set_io)
+  int64_t ldc = 0, ldf = 0;
+};
+}  // namespace mht
+
+struct mht_batch {
+  int n = 0;
+  std::vector<mht::BatchInst> inst;
+  std::vector<MhtBatchRec> recs[2];
+  std::vector<MhtBItem> items[2];
+  size_t recs_off[2] = {0, 0}, items_off[2] = {0, 0}, image_bytes = 0;
+  size_t counters_off = 0, counter_bytes = 0, status_off = 0, ws_bytes = 0;
+  int nctr = 0;
+  int slot_bytes = 0, nslot = 0, ldx_max = 0, rows_max = 0;
+  int tuned_nslot = 0, tuned_per_sm = 0;  // autotuned launch shape (0: defaults)
+  uint8_t* image_dev = nullptr;
+  uint8_t* ws_dev = nullptr;
+  bool bound = false, io_set = false;
+  int use_graph = 1;
+  mht::BatchGraph* graphs[3] = {nullptr, nullptr, nullptr};  // synthesis, analysis, weighted
+  ~mht_batch();
+};
+
+namespace mht {
+void batch_init(mht_batch& B, mht_plan* const* plans, int count, const int64_t* nrhs);
+void batch_fill_records(mht_batch& B);
+BatchLaunch batch_launch_desc(const mht_batch& B, int dir, bool weighted);
+}  // namespace mht

@@ -18,7 +18,8 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-constexpr size_t kTileBytes = 32 * 1024;    // target matrix bytes per per-stage work item
+constexpr size_t kTileBytes = 512 * 1024;   // target matrix bytes per per-stage work item
+constexpr int kItemRows = 512;               // and at most this many rows
 constexpr size_t kPItemBytes = 256 * 1024;  // largest persistent work item
 constexpr int kPItemRows = 1024;             // and at most this many rows (staged per item)
 constexpr size_t kSlotBytes = 32 * 1024;    // ring slot of the persistent kernel
@@ -155,7 +156,8 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
         const MhtBlockDesc& d = desc[dir][s][b];
         const int sib = (dir == 1 && s >= 1 && s <= L) ? int((b >> (L - s)) & 1) : 0;
         const size_t rowbytes = size_t(d.ldt) * es;
-        const int rpi = int(std::max<size_t>(1, rowbytes ? kTileBytes / rowbytes : size_t(1) << 20));
+        const int rpi = int(std::min<size_t>(kItemRows, std::max<size_t>(1, rowbytes ? kTileBytes / rowbytes
+                                                                                       : size_t(kItemRows))));
         if (d.rows == 0) {
           // adjoint of an ID block without T~ (full rank): still copies the skeleton out
           if (dir == 1 && s <= L && d.cols > 0) items[dir][s].push_back({int(b), 0, 0, sib});
@@ -165,10 +167,30 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
           const int cnt = std::min(rpi, d.rows - r0);
           items[dir][s].push_back({int(b), r0, cnt, sib});
           D.max_tile_bytes = std::max(D.max_tile_bytes, size_t(cnt) * rowbytes);
+          D.max_item_rows = std::max<int64_t>(D.max_item_rows, cnt);
         }
       }
       D.nitems = int64_t(items[dir][s].size());
     }
+
+  // tensor-core work items: 128-row tiles (skeleton-only items as for the SIMT lists)
+  std::vector<std::vector<MhtItem>> tcitems[2];
+  for (int dir = 0; dir < 2; ++dir) {
+    tcitems[dir].assign(nst, {});
+    for (int s = 0; s < nst; ++s) {
+      for (int64_t b = 0; b < nb; ++b) {
+        const MhtBlockDesc& d = desc[dir][s][b];
+        const int sib = (dir == 1 && s >= 1 && s <= L) ? int((b >> (L - s)) & 1) : 0;
+        if (d.rows == 0) {
+          if (dir == 1 && s <= L && d.cols > 0) tcitems[dir][s].push_back({int(b), 0, 0, sib});
+          continue;
+        }
+        for (int r0 = 0; r0 < d.rows; r0 += 128)
+          tcitems[dir][s].push_back({int(b), r0, std::min(128, d.rows - r0), sib});
+      }
+      P.st[s].dir[dir].tc_nitems = int64_t(tcitems[dir][s].size());
+    }
+  }
 
   // persistent work lists: dependency order (synthesis 0..L+1, analysis L+1..0), items of
   // at most kPItemBytes, and the number of items per (stage, block) as completion targets
@@ -215,6 +237,10 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
     for (int s = 0; s < nst; ++s) {
       P.st[s].dir[dir].items_off = pos;
       pos = align_up(pos + items[dir][s].size() * sizeof(MhtItem), 256);
+    }
+    for (int s = 0; s < nst; ++s) {
+      P.st[s].dir[dir].tc_items_off = pos;
+      pos = align_up(pos + tcitems[dir][s].size() * sizeof(MhtItem), 256);
     }
     P.fused[dir].targets_off = pos;
     pos = align_up(pos + targets[dir].size() * 4, 256);
@@ -265,6 +291,10 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
       if (!items[dir][s].empty())
         std::memcpy(img + P.st[s].dir[dir].items_off, items[dir][s].data(), items[dir][s].size() * sizeof(MhtItem));
     }
+    for (int s = 0; s < nst; ++s)
+      if (!tcitems[dir][s].empty())
+        std::memcpy(img + P.st[s].dir[dir].tc_items_off, tcitems[dir][s].data(),
+                    tcitems[dir][s].size() * sizeof(MhtItem));
     std::memcpy(img + P.fused[dir].targets_off, targets[dir].data(), targets[dir].size() * 4);
     if (!pitems[dir].empty())
       std::memcpy(img + P.fused[dir].items_off, pitems[dir].data(), pitems[dir].size() * sizeof(MhtPItem));

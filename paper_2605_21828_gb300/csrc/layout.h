@@ -40,6 +40,36 @@ struct MhtPItem {       // persistent work item: rows [start, start+count) of on
   int count;
 };
 
+// Batched apply of many plans in one persistent launch: one record per (instance, stage,
+// direction) with the device addresses its items read and write, and one item per work
+// item of any instance, in dependency order (all items of an instance's phase k precede its
+// phase k+1).
+struct MhtBatchRec {              // 128 bytes
+  unsigned long long data;        // matrices of the instance (its packed image, [data])
+  unsigned long long idx;         // its [index]
+  unsigned long long desc;        // block descriptors of this stage and direction
+  unsigned long long perm;        // its space permutation
+  unsigned long long wts;         // its weights (used when the launch asks for weights)
+  unsigned long long in0, in1;    // input vector (and sibling buffer for the adjoint)
+  unsigned long long out0, out1;  // output vector (and sibling buffer)
+  long long is_e, is_k, os_e, os_k;  // element strides (entry, right-hand side)
+  int nrhs;
+  int mode;                       // 0 synthesis ID, 1 adjoint ID, 2 synthesis U, 3 adjoint U
+  int cplx;                       // complex instance (interleaved float pairs)
+  int wait_ctr;                   // completion counter to wait for (-1: none)
+  unsigned wait_count;            // ... until it reaches this many items
+  int done_ctr;                   // counter this record's items increment when done
+};
+
+struct MhtBItem {       // 16 bytes
+  int rec;              // record index
+  int blk;              // block within the record's stage
+  int start;            // first row / column
+  int count_sib;        // count | (sibling buffer << 31)
+};
+
+static_assert(sizeof(MhtBatchRec) == 128, "batch record size");
+static_assert(sizeof(MhtBItem) == 16, "batch item size");
 static_assert(sizeof(MhtBlockDesc) == 32, "descriptor size");
 static_assert(sizeof(MhtPItem) == 16, "persistent item size");
 static_assert(sizeof(MhtItem) == 16, "item size");

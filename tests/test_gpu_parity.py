@@ -259,9 +259,9 @@ def test_launch_count_per_path(torch_cuda):
     from paper_2605_21828_gb300 import Plan
     F, _ = _sphere_factors(1000, 31, 64, 1e-6)
     plan = Plan.from_factors(oracle_to_arrays(F), mode="fp32")
+    assert 1 < plan.launch_count(1) <= F.L + 2  # automatic: one launch per stage
+    plan.set_path("fused")
     assert plan.launch_count(1) == 1  # one persistent launch runs every stage
-    plan.set_path("staged")
-    assert 1 < plan.launch_count(1) <= F.L + 2
 
 
 def test_repeated_applies_are_deterministic(torch_cuda):
@@ -277,3 +277,67 @@ def test_repeated_applies_are_deterministic(torch_cuda):
         assert torch.equal(plan.synthesize_raw(c), f0)
         assert torch.equal(plan.analyze_raw(f0), a0)
     assert plan.check() == 0
+
+
+@pytest.mark.parametrize("nrhs", [16, 37, 64, 130])
+def test_tensor_core_3xtf32_matches_oracle(torch_cuda, nrhs):
+    # 3xTF32 tcgen05 block products (hi*hi + hi*lo + lo*hi, FP32 accumulation) for >= 16 RHS
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    for n, lmax, leaf in ((1000, 31, 64), (4096, 63, 128)):
+        F, _ = _sphere_factors(n, lmax, leaf, 1e-6)
+        w = np.random.default_rng(2).uniform(0.5, 1.5, n)
+        plan = Plan.from_factors(oracle_to_arrays(F), mode="3xtf32", weights=w).bind(max_nrhs=nrhs)
+        C_ = W.gaussian_columns(F.m, nrhs, 31)
+        f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
+        assert plan.check() == 0
+        _check(f, B.synthesize(F, C_), "3xtf32")
+        G = W.gaussian_columns(n, nrhs, 41)
+        a = plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy()
+        assert plan.check() == 0
+        _check(a, B.analyze(F, G, w), "3xtf32")
+        fw = plan.synthesize_raw(_to_dev(torch, C_, plan), weighted=True).cpu().numpy()
+        _check(fw, w[:, None] * B.synthesize(F, C_), "3xtf32")
+
+
+@pytest.mark.parametrize("nrhs", [8, 16, 21, 40])
+def test_tensor_core_3xtf32_complex_matches_oracle(torch_cuda, nrhs):
+    # complex factors on the tensor cores: one real product of twice the width per block
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    F, _ = _torus_factors(1024, 1024, 64, 1e-6)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, F.n)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode="3xtf32", weights=w).bind(max_nrhs=nrhs)
+    C_ = W.gaussian_columns(F.m, nrhs, 51, complex_=True)
+    f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
+    assert plan.check() == 0
+    _check(f, B.synthesize(F, C_), "3xtf32")
+    G = W.gaussian_columns(F.n, nrhs, 61, complex_=True)
+    a = plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy()
+    assert plan.check() == 0
+    _check(a, B.analyze(F, G, w), "3xtf32")
+    # the same plan in FP32 SIMT arithmetic agrees
+    plan.set_mode("fp32")
+    f32 = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
+    _check(f32, B.synthesize(F, C_), "fp32")
+
+
+def test_autotuned_configurations_keep_parity(torch_cuda):
+    # the autotuner picks per-stage launch shapes (RHS tile, ring slots, CTAs per SM, tensor
+    # cores); applies with the tuned RHS count must still match the oracle
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    F, _ = _sphere_factors(4096, 63, 128, 1e-6)
+    w = np.random.default_rng(4).uniform(0.5, 1.5, F.n)
+    for mode, nrhs in (("fp32", 1), ("fp32", 5), ("3xtf32", 20), ("fp64", 3)):
+        plan = Plan.from_factors(oracle_to_arrays(F), mode=mode, weights=w).bind(max_nrhs=nrhs)
+        tuned = plan.autotune(nrhs)
+        assert len(tuned) == 2 * (plan.levels + 2)
+        assert all(t["ms"] > 0 for t in tuned)
+        if mode != "3xtf32":
+            assert not any(t["tensor"] for t in tuned)
+        C_ = W.gaussian_columns(F.m, nrhs, 71)
+        _check(plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy(), B.synthesize(F, C_), mode)
+        G = W.gaussian_columns(F.n, nrhs, 81)
+        _check(plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy(), B.analyze(F, G, w), mode)
+        assert plan.check() == 0

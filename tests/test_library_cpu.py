@@ -236,3 +236,52 @@ def test_blocked_randomized_pivoting_id_matches_dense(mht_lib):
         refa = Phi.T @ g
         assert np.linalg.norm(B.analyze(F, g) - refa) / np.linalg.norm(refa) < 10 * eps
     assert errs["blocked"] < 10 * eps and errs["classical"] < 10 * eps
+
+
+def test_clone_and_set_mode(mht_lib):
+    from paper_2605_21828_gb300 import MhtError
+    n = 256
+    X, Phi, lam = _sphere(n, 15)
+    p = _plan_cls().build(n=n, m=256, eigenvalues=lam, evaluator="sphere", points=X, eps=1e-6, leaf_size=32)
+    q = p.clone("fp64")
+    assert q.mode == "fp64" and q.info()["mode"] == 0
+    a, b = p.export(), q.export()
+    for k in a:
+        if isinstance(a[k], np.ndarray):
+            assert np.array_equal(a[k], b[k]), k
+    p.set_mode("3xtf32")
+    assert p.info()["mode"] == 2
+    p.set_mode("fp32")
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        q.set_mode("fp32")  # storage precision differs
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        p.set_mode("fp64")
+
+
+def test_batch_create_validates_and_counts_items(mht_lib):
+    import ctypes as C
+    from paper_2605_21828_gb300 import Batch, MhtError, _lib
+    X, Phi, lam = _sphere(512, 21)
+    a = _plan_cls().build(n=512, m=484, eigenvalues=lam[:484], evaluator="sphere", points=X, eps=1e-6, leaf_size=64)
+    Xt = W.torus_points(256)
+    K = W.torus_modes(256)
+    b = _plan_cls().build(n=256, m=256, eigenvalues=W.torus_eigenvalues(K), evaluator="torus", points=Xt,
+                          torus_modes=K, eps=1e-6, leaf_size=32)
+    bt = Batch([a, b], [3, 1])
+    ib, wb = bt.device_bytes()
+    assert ib > sum(p.device_bytes(1)[0] for p in (a, b)) // 2 and wb > 0
+    lib = _lib.load()
+    n0, n1 = C.c_int64(), C.c_int64()
+    _lib.check(lib.mht_batch_info(bt._h, C.byref(n0), C.byref(n1), None))
+    items = sum(sum(p.level_info(s)["items"] for s in range(p.levels + 2)) for p in (a, b)) \
+        if "items" in a.level_info(0) else None
+    assert n0.value > 0 and n1.value > 0
+    if items is not None:
+        assert n0.value == items
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        Batch([a, a.clone("fp64")], [1, 1])
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        Batch([a], [0])
+    st = lib.mht_batch_synthesize(bt._h, None)
+    assert st == 9  # not bound
+    bt.close()

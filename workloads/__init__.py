@@ -46,6 +46,21 @@ def torus_modes(m: int) -> np.ndarray:
     return np.stack([k1.ravel(), k2.ravel()], axis=1)
 
 
+def torus_modes_lowest(m: int) -> np.ndarray:
+    """The m integer frequencies of smallest |k|^2 (ties by k1, then k2), shape (m, 2), int64.
+
+    For any m (the box of :func:`torus_modes` needs a perfect square).
+    """
+    s = 2
+    while s * s < m:
+        s += 2
+    k = np.arange(-s // 2 - 1, s // 2 + 2, dtype=np.int64)
+    k1, k2 = np.meshgrid(k, k, indexing="ij")
+    K = np.stack([k1.ravel(), k2.ravel()], axis=1)
+    order = np.lexsort((K[:, 1], K[:, 0], K[:, 0] ** 2 + K[:, 1] ** 2))
+    return K[order[:m]]
+
+
 def torus_eigenvalues(modes: np.ndarray) -> np.ndarray:
     """|k|^2 for each integer frequency (the periodic Laplacian's eigenvalue)."""
     modes = np.asarray(modes, dtype=np.float64)
@@ -155,6 +170,14 @@ def deformed_icosphere(level: int, amplitude: float = 0.2, seed: int = 3):
     h = random_polynomial_height(V, 6, seed)
     r = 1.0 + amplitude * h / np.max(np.abs(h))
     return V * r[:, None], F
+
+
+def deformed_sphere_points(n: int, seed: int = 0, amplitude: float = 0.2, shape_seed: int = 3) -> np.ndarray:
+    """Jittered Fibonacci points moved to radius 1 + amplitude * h / max|h| (h as in
+    :func:`deformed_icosphere`), for deformed-sphere point sets of any size."""
+    X = fibonacci_points(n, seed=seed)
+    h = random_polynomial_height(X, 6, shape_seed)
+    return X * (1.0 + amplitude * h / np.max(np.abs(h)))[:, None]
 
 
 def batched_instances(count: int = 64, seed: int = 2, nmin: int = 2000, nmax: int = 40000,
