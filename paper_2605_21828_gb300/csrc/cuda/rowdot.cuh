@@ -343,6 +343,21 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
   const int nch = it.count == 0 ? 0 : (it.count + rpc - 1) / rpc;
   const int ntile = (a.nrhs + RT - 1) / RT;
   R* out = (MODE == ADJ_ID && it.sib) ? a.out1 : a.out0;
+  // every warp: lane 0 waits (bounded) for chunk g of the CTA's sequence and the warp follows
+  // its verdict; a warp that gave up clears the CTA's flag, and the next barrier makes every
+  // warp stop (the rows it computed meanwhile are unspecified, as the status bit reports)
+  auto wait_chunk = [&](unsigned g) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+      ok = mbar_wait_bounded(&sm.bar[g % unsigned(nslot)], (g / unsigned(nslot)) & 1u) ? 1 : 0;
+      if (!ok) {
+        atomicOr(status, 1u);
+        *flag = 0;
+      }
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+  };
 
   if (MODE == ADJ_ID || MODE == SYN_U)
     for (int ii = threadIdx.x; ii < it.count; ii += kThreads) {
@@ -398,7 +413,7 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
             ident[(t * rows_max + ii) * W + c] =
                 t < nk ? __ldcg(a.in0 + (sidx * a.is_e + (long long)(k0 + t) * a.is_k) * W + c) : R(0);
       }
-    __syncthreads();
+    __syncthreads();  // the tile's inputs are staged
     if (MODE == ADJ_ID && it.start == 0) {  // identity part: out[skel_j] = z_j
       for (int e = threadIdx.x; e < d.cols * nk; e += kThreads) {
         const int jj = e / nk, t = e % nk;
@@ -409,18 +424,11 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
       }
     }
     for (int ch = 0; ch < nch; ++ch) {
-      const unsigned g = cons;
-      const int slot = int(g % unsigned(nslot));
-      // one thread waits for the chunk; the CTA follows its verdict
-      if (threadIdx.x == 0 && copies && !mbar_wait_bounded(&sm.bar[slot], (g / unsigned(nslot)) & 1u)) {
-        atomicOr(status, 1u);
-        *flag = 0;
-      }
-      __syncthreads();
-      if (!*flag) return false;
+      const int slot = int(cons % unsigned(nslot));
+      const bool ready = !copies || wait_chunk(cons);  // each warp waits for the chunk itself
       const R* rows = reinterpret_cast<const R*>(sm.slots + size_t(slot) * sm.slot_bytes);
       const int cnt = min(rpc, it.count - ch * rpc);
-      for (int rr = warp; rr < cnt; rr += kWarps) {
+      for (int rr = ready ? warp : cnt; rr < cnt; rr += kWarps) {
         const int ii = ch * rpc + rr;  // row within the item
         const int i = it.start + ii;
         R acc[RT][W];
@@ -452,7 +460,10 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
           for (int c = 0; c < W; ++c) out[(dst * a.os_e + (long long)(k0 + t) * a.os_k) * W + c] = val[c];
         }
       }
-      __syncthreads();  // the slot (and, after the tile's last chunk, xs / ident) is free
+      // one barrier per chunk: the slot (and after the tile's last chunk, xs / ident) is free
+      // and thread 0 refills it at once
+      __syncthreads();
+      if (!*flag) return false;
       if (copies) {
         ++cons;
         if (threadIdx.x == 0) refill();

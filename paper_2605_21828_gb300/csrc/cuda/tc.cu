@@ -7,19 +7,19 @@
 // (Markidis et al. 2018; Ootomo & Yokota 2022); the dropped lo*lo term is below FP32
 // rounding.
 //
-// One CTA (4 warps) computes a 128-row tile of one block for N right-hand sides:
-//   * K is streamed in chunks of 32.  The matrix rows are read with 128-bit loads (one chunk
-//     ahead, in registers), the input rows are gathered per chunk; both are split into
+// One CTA (16 warps) computes a 128-row tile of one block for N right-hand sides:
+//   * K is streamed in chunks of 32.  The matrix rows (16-byte cp.async) and the gathered
+//     input entries (4-byte cp.async) arrive two chunks ahead in a raw ring; both are split into
 //     hi/lo and written to shared memory in the canonical no-swizzle K-major layout (core
 //     matrices of 8 rows x 16 bytes; 128 bytes between core matrices along K, 1024 along M/N).
 //   * One thread issues, per chunk, 4 x 3 tcgen05.mma.kind::tf32 (M = 128, K = 8 each): hi*hi
 //     into one 128 x N FP32 tensor-memory buffer, hi*lo + lo*hi into a second, both starting
 //     from zero, and commits them to the chunk's mbarrier.  A 2-stage shared-memory ring and
 //     two pairs of TMEM buffers let the loads of chunk c+1 overlap the MMAs of chunk c.
-//   * After a chunk's MMAs complete, every thread reads its row of both buffers
-//     (tcgen05.ld; thread i owns TMEM lane i = tile row i) and adds them to FP32 registers with
-//     round-to-nearest and Kahan compensation, so tensor-core accumulation never spans more
-//     than one chunk of K.
+//   * After a chunk's MMAs complete, every warp reads its rows of both buffers (tcgen05.ld;
+//     warp w owns TMEM lanes 32 (w % 4) .. + 31 = tile rows, and quarter w / 4 of the columns)
+//     and adds them to FP32 registers with round-to-nearest and Kahan compensation, so
+//     tensor-core accumulation never spans more than one chunk of K.
 //   * The epilogue adds the identity term of the interpolative decomposition and stores the row.
 // Every mbarrier wait is bounded in time; on timeout the kernel sets a status bit, skips the
 // remaining work, and still releases its tensor memory.
@@ -34,7 +34,8 @@
 namespace mht {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 512;  // 16 warps: TMEM lane quadrant = warp % 4, column quarter = warp / 4
+constexpr int kTcDepth = 3;      // raw chunk slots: chunks c, c+1, c+2 in flight
 constexpr int kTcM = 128;   // tile rows = tensor-memory lanes
 constexpr int kTcK = 32;    // K per pipeline stage (TF32 elements)
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
@@ -100,67 +101,57 @@ __device__ __forceinline__ void mma_tf32(unsigned tmem, uint64_t a, uint64_t b, 
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
-__device__ __forceinline__ float4 ldg_nc(const float* p) {
-  float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p));
-  return v;
+
+// 16-byte (A rows) and 4-byte (gathered B entries) asynchronous global -> shared copies; a
+// source size of 0 zero-fills the destination without reading (the address stays valid).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
-// Splits this thread's 8 float4 of a chunk into the hi / lo core-matrix tiles.
-__device__ __forceinline__ void store_a(const float4 (&r)[8], unsigned char* Ahi, unsigned char* Alo) {
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int q = threadIdx.x + kTcThreads * u;
-    const int m = q >> 3, c4 = q & 7;
-    const int off = (m >> 3) * 1024 + c4 * 128 + (m & 7) * 16;
-    float4 h, l;
-    split(r[u].x, h.x, l.x);
-    split(r[u].y, h.y, l.y);
-    split(r[u].z, h.z, l.z);
-    split(r[u].w, h.w, l.w);
-    *reinterpret_cast<float4*>(Ahi + off) = h;
-    *reinterpret_cast<float4*>(Alo + off) = l;
-  }
-}
-
-// Loads this thread's 8 float4 of a 128 x 32 chunk of the tile's rows (zero outside).
-// Complex factors are read as real rows of 2 ldt floats (re, im interleaved).
-template <int W>
-__device__ __forceinline__ void load_a(const TcParams& p, const MhtBlockDesc& d, const MhtItem& it, int k0,
-                                       float4 (&r)[8]) {
-  const int ldr = d.ldt * W;  // real row stride
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int q = threadIdx.x + kTcThreads * u;
-    const int m = q >> 3, c4 = q & 7, kk = k0 + c4 * 4;
-    r[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (m < it.count && kk < ldr)
-      r[u] = ldg_nc(p.data + (d.t_off + (long long)(it.start + m) * d.ldt) * W + kk);
-  }
-}
+// core-matrix byte offset of element group (row m, 4-column group c4) in a no-swizzle K-major
+// tile with 32 columns: 8 x 16-byte core matrices, 128 bytes apart along K, 1024 along M/N
+__device__ __forceinline__ int core_off(int m, int c4) { return (m >> 3) * 1024 + c4 * 128 + (m & 7) * 16; }
 
 // C: complex factors and vectors.  The complex product y = A x is computed as one real
 // product: A's interleaved storage is a real matrix of 2K columns, and column n of B holds
 // (xr, -xi) for output n < N/2 (the real parts) and (xi, xr) for output N/2 + n (the imaginary
 // parts), so a tile of N accumulator columns carries N/2 complex right-hand sides.
+//
+// Pipeline per chunk c (32 columns of K): the raw rows of A for chunk c + 2 and the gathered
+// B entries are requested with cp.async into a 3-slot raw ring (each thread copies, and later
+// converts, only its own elements, so no barrier separates the copy from the conversion);
+// chunk c is split into TF32 hi / lo operand tiles (2 stages), one thread issues its 12 MMAs,
+// and meanwhile every warp drains chunk c - 1 from tensor memory: warp w reads quarter w / 4 of
+// the accumulator columns for TMEM lane quadrant w % 4.
 template <int MODE, int N, bool C>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
   static_assert(N == 16 || N == 32 || N == 64, "RHS tile");
   constexpr int W = C ? 2 : 1;
-  constexpr int NR = N / W;  // right-hand sides per tile
+  constexpr int NR = N / W;   // right-hand sides per tile
+  constexpr int H = N / 4;    // accumulator columns drained per warp (one quarter)
   constexpr int A_BYTES = kTcM * kTcK * 4;
   constexpr int B_BYTES = N * kTcK * 4;
   constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int NB = MODE == TC_ADJ_ID ? 2 : 1;  // raw B buffers (input and sibling)
+  constexpr int RAW = A_BYTES + NB * B_BYTES;
   constexpr int NCOLS = 4 * N;  // two chunk buffers x (hi*hi sum, correction sum)
+  constexpr int BG = N * (kTcK / 4);  // 4-entry groups of a B chunk
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm);       // [2]
   unsigned* tmem_slot = reinterpret_cast<unsigned*>(sm + 64);
   volatile int* flag = reinterpret_cast<volatile int*>(sm + 68);
-  int* ksrc = reinterpret_cast<int*>(sm + 128);            // [2][kTcK]
-  float* kw = reinterpret_cast<float*>(sm + 384);          // [2][kTcK]
-  unsigned char* stages = sm + 1024;
+  int* ksrc = reinterpret_cast<int*>(sm + 128);            // [kTcDepth][kTcK]
+  float* kw = reinterpret_cast<float*>(sm + 512);          // [kTcDepth][kTcK]
+  unsigned char* stages = sm + 1024;                       // [2][STAGE]
+  unsigned char* raw = stages + 2 * STAGE;                 // [kTcDepth][RAW]
 
   const MhtItem it = p.items[blockIdx.x];
   const MhtBlockDesc d = p.desc[it.blk];
@@ -203,14 +194,67 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
   const unsigned tmem = *tmem_slot;
   // instruction descriptor: D = F32, A = B = TF32, both K-major, N >> 3, M >> 4
   const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | (unsigned(N >> 3) << 17) | (unsigned(kTcM >> 4) << 24);
+  const int ldr = d.ldt * W;  // real row stride of A
 
-  // Row accumulators in registers (thread = tile row = TMEM lane).  Each chunk's MMAs start
-  // from zero and its two partial sums are added here with FP32 round-to-nearest: the tensor
-  // core's own accumulation is not round-to-nearest, and over a long K its error would exceed
-  // the FP32 level that the split is meant to reach.
-  float acc[N], cmp[N];  // running sums and their Kahan compensation
+  // warp 0: sources (and weights) of chunk x's 32 real columns into ring slot x % kTcDepth
+  auto sources = [&](int x) {
+    const int kr = x * kTcK + (tid & 31);
+    const int kk = kr / W;  // complex: real column kr is part kr & 1 of entry kr >> 1
+    int src = -1;
+    float w = 1.f;
+    if (kr < K) {
+      if (MODE == TC_SYN_ID) src = p.idx[d.idx_off + d.rows + kk];
+      else if (MODE == TC_ADJ_ID) src = d.out_off + kk;
+      else if (MODE == TC_SYN_U) src = d.in_off + kk;
+      else {
+        src = p.perm[d.out_off + kk];
+        if (p.wts) w = p.wts[src];
+      }
+    }
+    ksrc[(x % kTcDepth) * kTcK + (tid & 31)] = src;
+    kw[(x % kTcDepth) * kTcK + (tid & 31)] = w;
+  };
+  // every thread: requests its elements of chunk x (A rows, gathered B entries) and commits
+  auto request = [&](int x) {
+    if (x < nchunks) {
+      unsigned char* rs = raw + (x % kTcDepth) * RAW;
 #pragma unroll
-  for (int j = 0; j < N; ++j) acc[j] = cmp[j] = 0.f;
+      for (int u = 0; u < A_BYTES / 16 / kTcThreads; ++u) {
+        const int q = tid + kTcThreads * u;
+        const int m = q >> 3, c4 = q & 7, kr = x * kTcK + c4 * 4;
+        const bool ok = m < it.count && kr < ldr;
+        const float* src = ok ? p.data + (d.t_off + (long long)(it.start + m) * d.ldt) * W + kr : p.data;
+        cp_async16(rs + q * 16, src, ok ? 16u : 0u);
+      }
+      const int* ks = ksrc + (x % kTcDepth) * kTcK;
+      for (int g = tid; g < BG; g += kTcThreads) {
+        const int n = g % N, c4 = g / N;
+        const int rn = C ? (n < NR ? n : n - NR) : n;  // right-hand side of column n
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int kl = c4 * 4 + j;
+          const int src = ks[kl];
+          const bool ok = src >= 0 && rn < nk;
+          long long a = 0;
+          if (ok) {
+            a = ((long long)src * p.is_e + (long long)(r0 + rn) * p.is_k) * W;
+            if (C) a += (n < NR) ? (kl & 1) : 1 - (kl & 1);  // (xr, -xi) / (xi, xr): component
+          }
+          cp_async4(rs + A_BYTES + (g * 4 + j) * 4, ok ? p.in0 + a : p.in0, ok ? 4u : 0u);
+          if (NB == 2)
+            cp_async4(rs + A_BYTES + B_BYTES + (g * 4 + j) * 4, (ok && p.in1) ? p.in1 + a : p.in0,
+                      (ok && p.in1) ? 4u : 0u);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  // Kahan-compensated row sums of this thread's quarter of the accumulator columns
+  float acc[H], cmp[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) acc[j] = cmp[j] = 0.f;
+  const int quarter = warp >> 2;
   int issued = 0, drained = 0;
   // waits for chunk j's MMAs and adds its sums to acc; frees stage and TMEM buffer j & 1
   auto drain = [&](int j) {
@@ -221,26 +265,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
     __syncthreads();
     if (*flag) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned base = tmem + (unsigned(warp * 32) << 16) + unsigned((j & 1) * 2 * N);
+      const unsigned base = tmem + (unsigned((warp & 3) * 32) << 16) + unsigned((j & 1) * 2 * N + quarter * H);
 #pragma unroll
-      for (int cb = 0; cb < N / 16; ++cb) {
-        unsigned r[16], q[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(base + cb * 16)
-            : "memory");
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
-              "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
-            : "r"(base + N + cb * 16)
-            : "memory");
+      for (int cb = 0; cb < H / 4; ++cb) {
+        unsigned r[4], q[4];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                     : "r"(base + cb * 4)
+                     : "memory");
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3])
+                     : "r"(base + N + cb * 4)
+                     : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int n = cb * 16 + jj;
+        for (int jj = 0; jj < 4; ++jj) {
+          const int n = cb * 4 + jj;
           const float y = (__uint_as_float(r[jj]) + __uint_as_float(q[jj])) - cmp[n];
           const float t = acc[n] + y;
           cmp[n] = (t - acc[n]) - y;
@@ -252,75 +292,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
     drained = j + 1;
   };
 
-  float4 ra[8];  // matrix rows of the next chunk, loaded one chunk ahead
-  if (nchunks > 0) load_a<W>(p, d, it, 0, ra);
+  // prologue: sources and requests of chunks 0 and 1
+  for (int x = 0; x < kTcDepth - 1; ++x) {
+    if (warp == 0 && x < nchunks) sources(x);
+    __syncthreads();
+    request(x);
+  }
   for (int c = 0; c < nchunks; ++c) {
     const int s = c & 1;  // stage and TMEM buffer; chunk c-2 used them and was drained already
     unsigned char* st = stages + s * STAGE;
-    float* Ahi = reinterpret_cast<float*>(st);
-    float* Alo = reinterpret_cast<float*>(st + A_BYTES);
-    float* Bhi = reinterpret_cast<float*>(st + 2 * A_BYTES);
-    float* Blo = reinterpret_cast<float*>(st + 2 * A_BYTES + B_BYTES);
-    const int k0 = c * kTcK;
-    if (warp == 0) {
-      // sources of this chunk's 32 real input columns (and their weights); complex: real
-      // column k is part k & 1 of entry k >> 1
-      const int kk = (k0 + (tid & 31)) / W;
-      int src = -1;
-      float w = 1.f;
-      if (k0 + (tid & 31) < K) {
-        if (MODE == TC_SYN_ID) src = p.idx[d.idx_off + d.rows + kk];
-        else if (MODE == TC_ADJ_ID) src = d.out_off + kk;
-        else if (MODE == TC_SYN_U) src = d.in_off + kk;
-        else {
-          src = p.perm[d.out_off + kk];
-          if (p.wts) w = p.wts[src];
-        }
-      }
-      ksrc[s * kTcK + (tid & 31)] = src;
-      kw[s * kTcK + (tid & 31)] = w;
-    }
+    unsigned char* Ahi = st;
+    unsigned char* Alo = st + A_BYTES;
+    unsigned char* Bhi = st + 2 * A_BYTES;
+    unsigned char* Blo = st + 2 * A_BYTES + B_BYTES;
+    if (warp == 0 && c + kTcDepth - 1 < nchunks) sources(c + kTcDepth - 1);
     __syncthreads();
     if (!*flag) break;
-    // A chunk (this thread's 8 float4, loaded one iteration earlier) -> hi / lo core matrices;
-    // then load the matrix rows of chunk c+1 into the registers just freed
-    store_a(ra, reinterpret_cast<unsigned char*>(Ahi), reinterpret_cast<unsigned char*>(Alo));
-    if (c + 1 < nchunks) load_a<W>(p, d, it, k0 + kTcK, ra);
-    // B chunk: N right-hand sides x 32 gathered input entries -> hi / lo core matrices
-    for (int q = tid; q < N * (kTcK / 4); q += kTcThreads) {
-      const int n = q % N, c4 = q / N;
-      float v[4];
+    request(c + kTcDepth - 1);
+    cp_async_wait<kTcDepth - 1>();  // this thread's copies of chunk c have landed
+    const unsigned char* rs = raw + (c % kTcDepth) * RAW;
+#pragma unroll
+    for (int u = 0; u < A_BYTES / 16 / kTcThreads; ++u) {
+      const int q = tid + kTcThreads * u;
+      const float4 v = *reinterpret_cast<const float4*>(rs + q * 16);
+      float4 h, l;
+      split(v.x, h.x, l.x);
+      split(v.y, h.y, l.y);
+      split(v.z, h.z, l.z);
+      split(v.w, h.w, l.w);
+      const int off = core_off(q >> 3, q & 7);
+      *reinterpret_cast<float4*>(Ahi + off) = h;
+      *reinterpret_cast<float4*>(Alo + off) = l;
+    }
+    const float* kwc = kw + (c % kTcDepth) * kTcK;
+    for (int g = tid; g < BG; g += kTcThreads) {
+      const int n = g % N, c4 = g / N;
+      float4 v = *reinterpret_cast<const float4*>(rs + A_BYTES + g * 16);
+      if (NB == 2) {
+        const float4 v1 = *reinterpret_cast<const float4*>(rs + A_BYTES + B_BYTES + g * 16);
+        v.x += v1.x;
+        v.y += v1.y;
+        v.z += v1.z;
+        v.w += v1.w;
+      }
+      float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int kk = c4 * 4 + j;
-        const int src = ksrc[s * kTcK + kk];
-        float x = 0.f;
-        const int rn = C ? (n < NR ? n : n - NR) : n;  // right-hand side of column n
-        if (src >= 0 && rn < nk) {
-          const long long a = ((long long)src * p.is_e + (long long)(r0 + rn) * p.is_k) * W;
-          if (C) {
-            // real part: (xr, -xi) against (Ar, Ai); imaginary part: (xi, xr)
-            const int part = (k0 + kk) & 1;
-            const int comp = (n < NR) ? part : 1 - part;
-            x = __ldcg(p.in0 + a + comp);
-            if (p.in1) x += __ldcg(p.in1 + a + comp);
-            if (n < NR && part == 1) x = -x;
-          } else {
-            x = __ldcg(p.in0 + a);
-            if (p.in1) x += __ldcg(p.in1 + a);
-          }
-          x *= kw[s * kTcK + kk];
-        }
-        v[j] = x;
+        x[j] *= kwc[c4 * 4 + j];
+        if (C && n < NR && ((c4 * 4 + j) & 1)) x[j] = -x[j];  // (xr, -xi)
       }
       float4 h, l;
-      split(v[0], h.x, l.x);
-      split(v[1], h.y, l.y);
-      split(v[2], h.z, l.z);
-      split(v[3], h.w, l.w);
-      const int off = (n >> 3) * 1024 + c4 * 128 + (n & 7) * 16;
-      *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Bhi) + off) = h;
-      *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Blo) + off) = l;
+      split(x[0], h.x, l.x);
+      split(x[1], h.y, l.y);
+      split(x[2], h.z, l.z);
+      split(x[3], h.w, l.w);
+      const int off = core_off(n, c4);
+      *reinterpret_cast<float4*>(Bhi + off) = h;
+      *reinterpret_cast<float4*>(Blo + off) = l;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -344,11 +372,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
     issued = c + 1;
     if (c >= 1) drain(c - 1);  // overlaps the MMAs of chunk c
   }
+  cp_async_wait<0>();  // no copy may still target shared memory when the CTA exits
   if (issued > drained) drain(issued - 1);
   // error path: committed MMAs must finish before tensor memory is released
   if (tid == 0 && !*flag && issued > 0) mbar_wait(&mbar[(issued - 1) & 1], unsigned(((issued - 1) >> 1) & 1));
 
-  const int m = tid;  // TMEM lane = tile row
+  const int m = (warp & 3) * 32 + (tid & 31);  // TMEM lane = tile row
   if (m < it.count) {
     const int i = it.start + m;
     long long dst;
@@ -366,16 +395,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
       dst = (long long)d.in_off + i;
     }
 #pragma unroll
-    for (int n = 0; n < NR; ++n) {
+    for (int j = 0; j < H; ++j) {
+      const int col = quarter * H + j;
+      const int c = C ? col / NR : 0;        // complex: real parts, then imaginary parts
+      const int n = C ? col % NR : col;      // right-hand side within the tile
       if (n < nk) {
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-          const int col = c * NR + n;
-          float v = acc[col] - cmp[col];
-          if (MODE == TC_SYN_ID) v += p.in0[(sidx * p.is_e + (long long)(r0 + n) * p.is_k) * W + c];
-          if (MODE == TC_SYN_U) v *= wrow;
-          out[(dst * p.os_e + (long long)(r0 + n) * p.os_k) * W + c] = v;
-        }
+        float v = acc[j] - cmp[j];
+        if (MODE == TC_SYN_ID) v += p.in0[(sidx * p.is_e + (long long)(r0 + n) * p.is_k) * W + c];
+        if (MODE == TC_SYN_U) v *= wrow;
+        out[(dst * p.os_e + (long long)(r0 + n) * p.os_k) * W + c] = v;
       }
     }
   }
@@ -389,7 +417,8 @@ template <int MODE, int N, bool C>
 int launch_n(const TcLaunch& a, std::string& err) {
   constexpr int STAGE = 2 * kTcM * kTcK * 4 + 2 * N * kTcK * 4;
   constexpr int NR = C ? N / 2 : N;
-  const size_t smem = 1024 + 2 * size_t(STAGE);
+  constexpr int RAW = kTcM * kTcK * 4 + (MODE == TC_ADJ_ID ? 2 : 1) * N * kTcK * 4;
+  const size_t smem = 1024 + 2 * size_t(STAGE) + size_t(kTcDepth) * RAW;
   auto kern = k_tc3<MODE, N, C>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) {
