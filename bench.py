@@ -176,6 +176,16 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x, dist, device="cpu"):
+    """The largest value of x over all ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def get_plan(args, dist, rank):
     import numpy as np
 
@@ -269,10 +279,7 @@ def run_ours(args):
     plan.profile(False)
     clk = clocks.stop(local)
     status = plan.check()
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / K
     value = world * K * nrhs / (ms_total / 1000.0)
 
@@ -335,10 +342,7 @@ def run_ours(args):
             host_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist, dev)
         e2e = {"value": world * K * nrhs / dt, "unit": "transforms/s",
                "h2d_bytes_per_step": (m + n) * 4 * nrhs, "d2h_bytes_per_step": (n + m) * 4 * nrhs,
                "api": "mht_synthesize_host + mht_analyze_host (pinned host buffers)"}

@@ -237,6 +237,38 @@ mht_status mht_plan_bind_device(mht_plan* plan, void* factor_dev, size_t factor_
 mht_status mht_synthesize(mht_plan* plan, const void* c_dev, int64_t ldc, void* f_dev,
                           int64_t ldf, int64_t nrhs, void* stream);
 
+/* f = Phi diag(s) c: synthesis of diagonally scaled coefficients, the scale s (device, m real
+ * entries in the plan's precision, caller's mode order) applied inside the leaf stage's gather
+ * (no extra pass).  With s = sqrt(S(lambda_k)) and c = white noise this samples a Gaussian
+ * random field of spectral density S (Sec. 7.2); with s = F(lambda_k) it applies a spectral
+ * filter to given coefficients.  Same layout rules as mht_synthesize. */
+mht_status mht_synthesize_scaled(mht_plan* plan, const void* c_dev, int64_t ldc, const void* scale_dev,
+                                 void* f_dev, int64_t ldf, int64_t nrhs, void* stream);
+
+/* f_out = Phi diag(F) Phi^H W f_in (weighted != 0; Phi^H f_in otherwise): spectral filtering of
+ * point values (Sec. 7.1), or the covariance product Phi S Phi^H of Sec. 7.2.  Analysis, the diagonal
+ * (fused into synthesis' leaf stage) and synthesis run as one CUDA graph, captured on the first
+ * call with these arguments and replayed by later calls with the same ones (pointers, leading
+ * dimensions, RHS count, weighting, apply mode and autotuning state).  F: device, m real entries
+ * in the plan's precision, caller's mode order.  The coefficients pass through the workspace's
+ * host-staging area, so a filter call must not overlap a host-buffer transform on the plan.
+ * f_in and f_out: n x nrhs, must not alias.  Errors as mht_synthesize. */
+mht_status mht_filter(mht_plan* plan, const void* f_in_dev, int64_t ldi, void* f_out_dev, int64_t ldo,
+                      int64_t nrhs, const void* filter_dev, int32_t weighted, void* stream);
+
+/* Inverse transform (Sec. 7.1, Eq. inverse-MHT): c = argmin_c ||Phi c - f||_2 for each of the
+ * nrhs columns, by LSQR (Paige & Saunders 1982) on the butterfly apply: one synthesis and one
+ * analysis per iteration, FP64 scalar recurrences on the host.  A column stops when its
+ * residual estimate falls below tol * ||f|| or its normal-equation residual estimate
+ * ||Phi^H r|| below tol * ||Phi|| ||r||, or after max_iter iterations.  scratch_dev: caller
+ * device memory of mht_lsqr_scratch_bytes, 256-byte aligned.  Synchronizes `stream` every
+ * iteration.  *iters (optional): iterations run; *relres (optional): the largest final
+ * ||r|| / ||f|| estimate over the columns.  Layout and errors as mht_analyze. */
+mht_status mht_lsqr_scratch_bytes(const mht_plan* plan, int64_t nrhs, size_t* bytes);
+mht_status mht_inverse_lsqr(mht_plan* plan, const void* f_dev, int64_t ldf, void* c_dev, int64_t ldc,
+                            int64_t nrhs, void* scratch_dev, size_t scratch_bytes, int32_t max_iter,
+                            double tol, void* stream, int32_t* iters, double* relres);
+
 /* f = diag(w) Phi c: synthesis followed by the analysis weights (the adjoint of weighted
  * analysis, used for its gradient).  Same layout rules as mht_synthesize. */
 mht_status mht_synthesize_weighted(mht_plan* plan, const void* c_dev, int64_t ldc, void* f_dev,

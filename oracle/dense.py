@@ -45,3 +45,9 @@ def analyze_columns(col_eval, f: np.ndarray, cols: np.ndarray, w: np.ndarray | N
     for s in range(0, len(cols), chunk):
         out.append(col_eval(cols[s:s + chunk]).conj().T @ g)
     return np.concatenate(out, axis=0)
+
+
+def inverse(Phi: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """The inverse transform c = argmin_c ||Phi c - f||_2 (Sec. 7.1, Eq. inverse-MHT), by the
+    library least-squares routine (SVD-based), column by column for f (n, k)."""
+    return np.linalg.lstsq(Phi, f, rcond=None)[0]

@@ -74,6 +74,14 @@ SIGNATURES = {
     "mht_synthesize": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]),
     "mht_synthesize_weighted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
                                           C.c_void_p]),
+    "mht_synthesize_scaled": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64,
+                                        C.c_int64, C.c_void_p]),
+    "mht_filter": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                             C.c_int32, C.c_void_p]),
+    "mht_lsqr_scratch_bytes": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_size_t)]),
+    "mht_inverse_lsqr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                   C.c_size_t, C.c_int32, C.c_double, C.c_void_p, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_double)]),
     "mht_analyze": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
                               C.c_void_p]),
     "mht_synthesize_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,

@@ -336,6 +336,55 @@ class Plan:
                                     1 if weighted else 0, stream))
         return out[0] if vec else out.t()
 
+    def _real_vector(self, v, length, name):
+        import torch
+        rdt = torch.float64 if self.mode == "fp64" else torch.float32
+        if v.dtype != rdt or not v.is_cuda or v.numel() != length:
+            raise ValueError(f"{name} must be a CUDA {rdt} vector of {length} entries")
+        return v.contiguous()
+
+    def synthesize_scaled(self, c, scale):
+        """f = Phi diag(scale) c, the scale fused into the leaf stage (GRF sampling, filters)."""
+        import torch
+        lib = L.load()
+        buf, k, vec = self._colmajor(c, self.m)
+        s = self._real_vector(scale, self.m, "scale")
+        out = torch.empty((k, self.n), dtype=self.dtype, device=c.device)
+        st = C.c_void_p(torch.cuda.current_stream(c.device).cuda_stream)
+        L.check(lib.mht_synthesize_scaled(self._h, C.c_void_p(buf.data_ptr()), self.m, C.c_void_p(s.data_ptr()),
+                                          C.c_void_p(out.data_ptr()), self.n, k, st))
+        return out[0] if vec else out.t()
+
+    def filter(self, f, filt, weighted: bool = True):
+        """Phi diag(filt) Phi^H W f as one CUDA graph (analysis, fused diagonal, synthesis)."""
+        import torch
+        lib = L.load()
+        buf, k, vec = self._colmajor(f, self.n)
+        s = self._real_vector(filt, self.m, "filter")
+        out = torch.empty((k, self.n), dtype=self.dtype, device=f.device)
+        st = C.c_void_p(torch.cuda.current_stream(f.device).cuda_stream)
+        L.check(lib.mht_filter(self._h, C.c_void_p(buf.data_ptr()), self.n, C.c_void_p(out.data_ptr()), self.n, k,
+                               C.c_void_p(s.data_ptr()), 1 if weighted else 0, st))
+        return out[0] if vec else out.t()
+
+    def inverse(self, f, max_iter: int = 100, tol: float = 1e-6):
+        """c = argmin ||Phi c - f||_2 by LSQR on the fast transform; returns (c, iterations,
+        largest relative residual estimate)."""
+        import torch
+        lib = L.load()
+        buf, k, vec = self._colmajor(f, self.n)
+        nb = C.c_size_t()
+        L.check(lib.mht_lsqr_scratch_bytes(self._h, k, C.byref(nb)))
+        scratch = torch.empty(nb.value + 256, dtype=torch.uint8, device=f.device)
+        sp = (scratch.data_ptr() + 255) // 256 * 256
+        out = torch.empty((k, self.m), dtype=self.dtype, device=f.device)
+        it, rr = C.c_int32(), C.c_double()
+        st = C.c_void_p(torch.cuda.current_stream(f.device).cuda_stream)
+        L.check(lib.mht_inverse_lsqr(self._h, C.c_void_p(buf.data_ptr()), self.n, C.c_void_p(out.data_ptr()), self.m,
+                                     k, C.c_void_p(sp), nb.value, int(max_iter), float(tol), st, C.byref(it),
+                                     C.byref(rr)))
+        return (out[0] if vec else out.t()), int(it.value), float(rr.value)
+
     def synthesize_raw(self, c, weighted: bool = False):
         return self._apply(c, True, weighted)
 

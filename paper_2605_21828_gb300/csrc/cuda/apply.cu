@@ -663,10 +663,11 @@ int run_stage(const Ctx& c, int s, int mode, const void* in0, const void* in1, l
 // The stages of one direction in apply order: synthesis V, R (l = 1..L), U; the adjoint U^H,
 // R^H (l = L..1), V^H.  cfg(dir, s) gives each stage's configuration.
 template <class R, bool C, class Cfg>
-int synth_stages(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool weighted, Cfg&& cfg) {
+int synth_stages(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool weighted, Cfg&& cfg,
+                 const void* scale = nullptr) {
   const int L = c.F.L;
   const long long nr = c.nrhs;
-  int rc = run_stage<R, C>(c, 0, SYN_ID, cin, nullptr, 1, ldc, lvl(c, 0, 0), nullptr, nr, 1, nullptr, cfg(0, 0));
+  int rc = run_stage<R, C>(c, 0, SYN_ID, cin, nullptr, 1, ldc, lvl(c, 0, 0), nullptr, nr, 1, scale, cfg(0, 0));
   for (int l = 1; l <= L && !rc; ++l)
     rc = run_stage<R, C>(c, l, SYN_ID, lvl(c, 0, l - 1), nullptr, nr, 1, lvl(c, 0, l), nullptr, nr, 1, nullptr,
                          cfg(0, l));
@@ -836,7 +837,13 @@ StageCfg stage_cfg(const Ctx& c, int dir, int s, int default_rt) {
 }
 
 template <class R, bool C>
-int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool wt) {
+int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool wt,
+                   const void* scale = nullptr) {
+  if (scale) {  // the fused kernel has no input scale: per-stage launches
+    const int rt = pick_rt(c, 0);
+    return synth_stages<R, C>(c, cin, ldc, f, ldf, wt, [&](int dir, int s) { return stage_cfg(c, dir, s, rt); },
+                              scale);
+  }
   if (!use_tc(c) && (c.d.path == 2 || c.d.tune_nrhs != c.nrhs))
     if (const int rt = fused_rt(c, 0)) {
       const int rc = fused_dispatch<R, C, 0>(c, rt, cin, ldc, f, ldf, wt);
@@ -981,12 +988,70 @@ int autotune(Ctx& c, DeviceView& dv, std::vector<TuneRecord>* report) {
 
 int apply_synthesize(const Factorization& F, const Packed& P, const DeviceView& d, const void* c, int64_t ldc,
                      void* f, int64_t ldf, int64_t nrhs, bool wt, mht_apply_mode mode, void* stream,
-                     std::string& err) {
+                     std::string& err, const void* scale) {
   Ctx x{F, P, d, static_cast<cudaStream_t>(stream), nrhs, err, mode};
   if (P.fp64)
-    return P.cplx ? synth_dispatch<double, true>(x, c, ldc, f, ldf, wt)
-                  : synth_dispatch<double, false>(x, c, ldc, f, ldf, wt);
-  return P.cplx ? synth_dispatch<float, true>(x, c, ldc, f, ldf, wt) : synth_dispatch<float, false>(x, c, ldc, f, ldf, wt);
+    return P.cplx ? synth_dispatch<double, true>(x, c, ldc, f, ldf, wt, scale)
+                  : synth_dispatch<double, false>(x, c, ldc, f, ldf, wt, scale);
+  return P.cplx ? synth_dispatch<float, true>(x, c, ldc, f, ldf, wt, scale)
+                : synth_dispatch<float, false>(x, c, ldc, f, ldf, wt, scale);
+}
+
+struct FilterGraph {
+  const void *f_in = nullptr, *filter = nullptr;
+  void* f_out = nullptr;
+  int64_t ldi = 0, ldo = 0, nrhs = 0, tune_nrhs = 0;
+  bool weighted = false;
+  mht_apply_mode mode = MHT_APPLY_FP32;
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void filter_graph_destroy(FilterGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->capture) cudaStreamDestroy(g->capture);
+  delete g;
+}
+
+int apply_filter(const Factorization& F, const Packed& P, DeviceView& d, const void* f_in, int64_t ldi, void* f_out,
+                 int64_t ldo, int64_t nrhs, const void* filter, bool weighted, mht_apply_mode mode, void* stream,
+                 std::string& err) {
+  FilterGraph* g = d.filter;
+  const bool same = g && g->exec && g->f_in == f_in && g->filter == filter && g->f_out == f_out && g->ldi == ldi &&
+                    g->ldo == ldo && g->nrhs == nrhs && g->weighted == weighted && g->mode == mode &&
+                    g->tune_nrhs == d.tune_nrhs;
+  if (!same) {
+    if (!g) g = d.filter = new FilterGraph();
+    if (g->exec) {
+      cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+    }
+    if (!g->capture)
+      if (int rc = check(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking), err, "filter stream")) return rc;
+    // coefficients in the host-staging area for c (m x max_nrhs, leading dimension m)
+    void* coef = d.ws + 3 * P.ws_vec_bytes(d.max_nrhs);
+    if (int rc = check(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal), err, "filter capture"))
+      return rc;
+    int rc = apply_analyze(F, P, d, f_in, ldi, coef, F.m, nrhs, weighted, mode, g->capture, err);
+    if (!rc) rc = apply_synthesize(F, P, d, coef, F.m, f_out, ldo, nrhs, false, mode, g->capture, err, filter);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(g->capture, &graph);
+    if (!rc && e != cudaSuccess) rc = check(e, err, "filter capture end");
+    if (!rc) rc = check(cudaGraphInstantiate(&g->exec, graph, 0), err, "filter graph");
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) return rc;
+    g->f_in = f_in;
+    g->filter = filter;
+    g->f_out = f_out;
+    g->ldi = ldi;
+    g->ldo = ldo;
+    g->nrhs = nrhs;
+    g->weighted = weighted;
+    g->mode = mode;
+    g->tune_nrhs = d.tune_nrhs;
+  }
+  return check(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), err, "filter launch");
 }
 
 int apply_autotune(const Factorization& F, const Packed& P, DeviceView& d, int64_t nrhs, mht_apply_mode mode,

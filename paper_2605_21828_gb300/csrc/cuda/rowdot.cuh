@@ -217,7 +217,7 @@ __device__ __forceinline__ void row_dot(const R* __restrict__ row, const R* __re
 // ---------------------------------------------------------------------------------------
 // out[o(i)] = ident(i) + sum_j M[i, j] x[j] for the rows i of one work item.
 //   SYN_ID: M = T~ (r x K'),           x[j] = in[idx[r + j]],   o(i) = out_off + i,
-//           ident(i) = in[idx[i]]
+//           ident(i) = in[idx[i]]  (times w[idx[.]] when a scale is given: leaf stage only)
 //   ADJ_ID: M = conj(T~)^T (K' x r),   x[j] = z0[out_off + j] (+ z1[...]),
 //           o(i) = idx[r + i] in the sibling buffer; skeleton out[idx[j]] = x[j]
 //   SYN_U:  M = U (|tau| x r_L),       x[j] = yL[in_off + j],   o(i) = perm[out_off + i]
@@ -381,7 +381,10 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
       long long src = -1;
       R w = R(1);
       if (jj < d.cols) {
-        if (MODE == SYN_ID) src = a.idx[d.idx_off + d.rows + jj];
+        if (MODE == SYN_ID) {
+          src = a.idx[d.idx_off + d.rows + jj];
+          if (a.wts) w = a.wts[src];  // leaf stage: diagonal scale of the coefficients
+        }
         else if (MODE == ADJ_ID) src = (long long)d.out_off + jj;
         else if (MODE == SYN_U) src = (long long)d.in_off + jj;
         else {
@@ -406,12 +409,13 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
     if (MODE == SYN_ID)
       for (int ii = threadIdx.x; ii < it.count; ii += kThreads) {
         const long long sidx = a.idx[d.idx_off + it.start + ii];
+        const R sw = a.wts ? a.wts[sidx] : R(1);
 #pragma unroll
         for (int t = 0; t < RT; ++t)
 #pragma unroll
           for (int c = 0; c < W; ++c)
             ident[(t * rows_max + ii) * W + c] =
-                t < nk ? __ldcg(a.in0 + (sidx * a.is_e + (long long)(k0 + t) * a.is_k) * W + c) : R(0);
+                t < nk ? sw * __ldcg(a.in0 + (sidx * a.is_e + (long long)(k0 + t) * a.is_k) * W + c) : R(0);
       }
     __syncthreads();  // the tile's inputs are staged
     if (MODE == ADJ_ID && it.start == 0) {  // identity part: out[skel_j] = z_j

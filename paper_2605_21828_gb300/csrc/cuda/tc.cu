@@ -203,7 +203,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
     int src = -1;
     float w = 1.f;
     if (kr < K) {
-      if (MODE == TC_SYN_ID) src = p.idx[d.idx_off + d.rows + kk];
+      if (MODE == TC_SYN_ID) {
+        src = p.idx[d.idx_off + d.rows + kk];
+        if (p.wts) w = p.wts[src];  // leaf stage: diagonal scale of the coefficients
+      }
       else if (MODE == TC_ADJ_ID) src = d.out_off + kk;
       else if (MODE == TC_SYN_U) src = d.in_off + kk;
       else {
@@ -401,7 +404,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
       const int n = C ? col % NR : col;      // right-hand side within the tile
       if (n < nk) {
         float v = acc[j] - cmp[j];
-        if (MODE == TC_SYN_ID) v += p.in0[(sidx * p.is_e + (long long)(r0 + n) * p.is_k) * W + c];
+        if (MODE == TC_SYN_ID)
+          v += (p.wts ? p.wts[sidx] : 1.f) * p.in0[(sidx * p.is_e + (long long)(r0 + n) * p.is_k) * W + c];
         if (MODE == TC_SYN_U) v *= wrow;
         out[(dst * p.os_e + (long long)(r0 + n) * p.os_k) * W + c] = v;
       }

@@ -281,6 +281,62 @@ mht_status mht_synthesize(mht_plan* plan, const void* c_dev, int64_t ldc, void* 
   });
 }
 
+mht_status mht_synthesize_scaled(mht_plan* plan, const void* c_dev, int64_t ldc, const void* scale_dev, void* f_dev,
+                                 int64_t ldf, int64_t nrhs, void* stream) {
+  return guarded([&]() -> mht_status {
+    check_apply(plan, c_dev, ldc, plan ? plan->F.m : 0, f_dev, ldf, plan ? plan->F.n : 0, nrhs);
+    if (!scale_dev) mht::fail(MHT_ERR_INVALID_ARG, "NULL scale");
+    std::string err;
+    int rc = mht::apply_synthesize(plan->F, plan->P, plan->dev, c_dev, ldc, f_dev, ldf, nrhs, false, plan->mode, stream,
+                                   err, scale_dev);
+    if (rc) mht::fail(mht_status(rc), err);
+    return MHT_OK;
+  });
+}
+
+mht_status mht_filter(mht_plan* plan, const void* f_in_dev, int64_t ldi, void* f_out_dev, int64_t ldo, int64_t nrhs,
+                      const void* filter_dev, int32_t weighted, void* stream) {
+  return guarded([&]() -> mht_status {
+    check_apply(plan, f_in_dev, ldi, plan ? plan->F.n : 0, f_out_dev, ldo, plan ? plan->F.n : 0, nrhs);
+    if (!filter_dev) mht::fail(MHT_ERR_INVALID_ARG, "NULL filter");
+    if (f_in_dev == f_out_dev) mht::fail(MHT_ERR_INVALID_ARG, "f_in and f_out must not alias");
+    std::string err;
+    int rc = mht::apply_filter(plan->F, plan->P, plan->dev, f_in_dev, ldi, f_out_dev, ldo, nrhs, filter_dev,
+                               weighted != 0, plan->mode, stream, err);
+    if (rc) mht::fail(mht_status(rc), err);
+    return MHT_OK;
+  });
+}
+
+mht_status mht_lsqr_scratch_bytes(const mht_plan* plan, int64_t nrhs, size_t* bytes) {
+  return guarded([&]() -> mht_status {
+    if (!plan || !bytes || nrhs < 1) mht::fail(MHT_ERR_INVALID_ARG, "bad argument");
+    *bytes = mht::lsqr_scratch_bytes(plan->P, plan->F.n, plan->F.m, nrhs);
+    return MHT_OK;
+  });
+}
+
+mht_status mht_inverse_lsqr(mht_plan* plan, const void* f_dev, int64_t ldf, void* c_dev, int64_t ldc, int64_t nrhs,
+                            void* scratch_dev, size_t scratch_bytes, int32_t max_iter, double tol, void* stream,
+                            int32_t* iters, double* relres) {
+  return guarded([&]() -> mht_status {
+    check_apply(plan, f_dev, ldf, plan ? plan->F.n : 0, c_dev, ldc, plan ? plan->F.m : 0, nrhs);
+    if (!scratch_dev || scratch_bytes < mht::lsqr_scratch_bytes(plan->P, plan->F.n, plan->F.m, nrhs))
+      mht::fail(MHT_ERR_INVALID_ARG, "scratch smaller than mht_lsqr_scratch_bytes");
+    if (reinterpret_cast<uintptr_t>(scratch_dev) & 255) mht::fail(MHT_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+    if (max_iter < 0 || !(tol >= 0)) mht::fail(MHT_ERR_INVALID_ARG, "bad iteration limit or tolerance");
+    std::string err;
+    int it = 0;
+    double rr = 0;
+    int rc = mht::apply_lsqr(plan->F, plan->P, plan->dev, f_dev, ldf, c_dev, ldc, nrhs, scratch_dev, max_iter, tol,
+                             plan->mode, stream, &it, &rr, err);
+    if (rc) mht::fail(mht_status(rc), err);
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return MHT_OK;
+  });
+}
+
 mht_status mht_synthesize_weighted(mht_plan* plan, const void* c_dev, int64_t ldc, void* f_dev, int64_t ldf,
                                    int64_t nrhs, void* stream) {
   return guarded([&]() -> mht_status {

@@ -164,13 +164,24 @@ struct DeviceView {
   int64_t tune_nrhs = 0;          // RHS count the stage configurations were tuned for (0: none)
   mht_apply_mode tune_mode = MHT_APPLY_FP32;
   std::vector<StageCfg> tune[2];  // per direction and stage
+  struct FilterGraph* filter = nullptr;  // cached CUDA graph of the last spectral filter call
 };
+void filter_graph_destroy(FilterGraph* g);
+// f_out = Phi diag(filter) Phi^H [W] f_in in one CUDA graph (captured on the first call with
+// these arguments, replayed afterwards); the coefficients pass through the workspace's
+// host-staging area for c.
+int apply_filter(const Factorization& F, const Packed& P, DeviceView& d, const void* f_in, int64_t ldi, void* f_out,
+                 int64_t ldo, int64_t nrhs, const void* filter, bool weighted, mht_apply_mode mode, void* stream,
+                 std::string& err);
 Profiler* profiler_create();
 void profiler_destroy(Profiler* p);
 int profiler_read(Profiler* p, int direction, int nstages, double* ms, int64_t* launches, std::string& err);
+// scale (optional, device, m real entries in the plan's precision, caller's mode order):
+// f = Phi diag(scale) c, the scale fused into the leaf stage's gather.
 int apply_synthesize(const Factorization& F, const Packed& P, const DeviceView& d,
                      const void* c, int64_t ldc, void* f, int64_t ldf, int64_t nrhs,
-                     bool weighted, mht_apply_mode mode, void* stream, std::string& err);
+                     bool weighted, mht_apply_mode mode, void* stream, std::string& err,
+                     const void* scale = nullptr);
 int apply_analyze(const Factorization& F, const Packed& P, const DeviceView& d, const void* f,
                   int64_t ldf, void* c, int64_t ldc, int64_t nrhs, bool weighted,
                   mht_apply_mode mode, void* stream, std::string& err);
@@ -211,6 +222,13 @@ int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void
 // Copies the device status word to *flags, clears it, and synchronizes the stream.
 int device_status(void* status_dev, void* stream, unsigned* flags, std::string& err);
 
+// Inverse transform by LSQR (lsqr.cu): c = argmin ||Phi c - f||_2 per column; scratch of
+// lsqr_scratch_bytes in caller device memory; synchronous on `stream`.
+size_t lsqr_scratch_bytes(const Packed& P, int64_t n, int64_t m, int64_t k);
+int apply_lsqr(const Factorization& F, const Packed& P, const DeviceView& d, const void* f, int64_t ldf, void* c,
+               int64_t ldc, int64_t k, void* scratch, int max_iter, double tol, mht_apply_mode mode, void* stream,
+               int* iters, double* relres, std::string& err);
+
 // Batched apply of many FP32 plans in one persistent launch (batch.cu).
 struct BatchLaunch {
   const void* recs;         // MhtBatchRec[] of the direction (device)
@@ -246,7 +264,10 @@ struct mht_plan {
   mht::DeviceView dev;
   std::vector<mht::TuneRecord> tune_report;
   bool bound = false;
-  ~mht_plan() { mht::profiler_destroy(dev.prof); }
+  ~mht_plan() {
+    mht::profiler_destroy(dev.prof);
+    mht::filter_graph_destroy(dev.filter);
+  }
 };
 
 // A batch of FP32 plans applied together (batch.cpp, batch.cu).

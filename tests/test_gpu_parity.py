@@ -341,3 +341,61 @@ def test_autotuned_configurations_keep_parity(torch_cuda):
         G = W.gaussian_columns(F.n, nrhs, 81)
         _check(plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy(), B.analyze(F, G, w), mode)
         assert plan.check() == 0
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_scaled_synthesis_and_spectral_filter_match_oracle(torch_cuda, mode):
+    # f = Phi diag(s) c with the scale fused into the leaf stage; Phi diag(F) Phi^H W f as one
+    # CUDA graph, replayed with new filter values behind the same device pointer
+    import ctypes as C
+    from paper_2605_21828_gb300 import Plan, _lib
+    torch = torch_cuda
+    rdt = torch.float64 if mode == "fp64" else torch.float32
+    for F, w in ((_sphere_factors(4096, 63, 128, 1e-6)[0], None), (_torus_factors(1024, 1024, 64, 1e-10)[0], 1)):
+        n, m = F.n, F.m
+        wts = np.random.default_rng(5).uniform(0.5, 1.5, n)
+        plan = Plan.from_factors(oracle_to_arrays(F), mode=mode, weights=wts).bind(max_nrhs=3)
+        s = np.random.default_rng(6).uniform(0.1, 2.0, m)
+        C_ = W.gaussian_columns(m, 3, 7, complex_=F.complex_)
+        got = plan.synthesize_scaled(_to_dev(torch, C_, plan), torch.from_numpy(s).to(rdt).cuda()).cpu().numpy()
+        _check(got, B.synthesize(F, s[:, None] * C_), mode)
+        # raw ABI, fixed buffers: capture once, replay, replay with a changed filter
+        k = 2
+        G = W.gaussian_columns(n, k, 8, complex_=F.complex_)
+        fin = torch.from_numpy(np.ascontiguousarray(G.T)).to(plan.dtype).cuda()  # (k, n) = column-major n x k
+        fout = torch.zeros_like(fin)
+        filt = torch.from_numpy(s).to(rdt).cuda()
+        st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        lib = _lib.load()
+        for rep in range(3):
+            if rep == 2:
+                filt.mul_(0.5).add_(0.25)
+            _lib.check(lib.mht_filter(plan._h, C.c_void_p(fin.data_ptr()), n, C.c_void_p(fout.data_ptr()), n, k,
+                                      C.c_void_p(filt.data_ptr()), 1, st))
+            fv = filt.double().cpu().numpy()
+            ref = B.synthesize(F, fv[:, None] * B.analyze(F, G, wts))
+            _check(fout.t().cpu().numpy(), ref, mode)
+        assert plan.check() == 0
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_inverse_lsqr_matches_least_squares_solution(torch_cuda, mode):
+    # Eq. inverse-MHT solved by LSQR on the GPU apply, against the oracle's least-squares
+    # solution for the same (butterfly) operator; real sphere and complex torus
+    from oracle import dense as D
+    from paper_2605_21828_gb300 import Plan
+    torch = torch_cuda
+    cases = ((_sphere_factors(4096, 31, 128, 1e-6)[0], False), (_torus_factors(1024, 256, 64, 1e-10)[0], True))
+    for F, cplx in cases:
+        A = B.to_dense(F)
+        c0 = W.gaussian_columns(F.m, 3, 11, complex_=cplx)
+        f = A @ c0 + 0.01 * W.gaussian_columns(F.n, 3, 12, complex_=cplx)
+        ref = D.inverse(A, f)
+        plan = Plan.from_factors(oracle_to_arrays(F), mode=mode).bind(max_nrhs=3)
+        tol = 1e-12 if mode == "fp64" else 1e-7
+        c, iters, rr = plan.inverse(_to_dev(torch, f, plan), max_iter=300, tol=tol)
+        assert plan.check() == 0 and 0 < iters <= 300
+        err = np.linalg.norm(c.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert err.max() <= (1e-9 if mode == "fp64" else 2e-5), err
+        res = np.linalg.norm(A @ ref - f, axis=0) / np.linalg.norm(f, axis=0)
+        assert rr <= res.max() * 1.01 + 1e-6

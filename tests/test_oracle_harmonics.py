@@ -105,3 +105,17 @@ def test_sphere_is_laplacian_eigenfunction():
     d2p = (Y(th, ph + h) - 2 * Y(th, ph) + Y(th, ph - h)) / h ** 2
     lap = d2t + np.cos(th) / np.sin(th) * dt + d2p / np.sin(th) ** 2
     assert np.allclose(lap, -l * (l + 1) * Y(th, ph), atol=1e-4)
+
+
+def test_inverse_transform_recovers_coefficients_and_solves_normal_equations():
+    # Eq. inverse-MHT: a consistent system returns its coefficients; an inconsistent one
+    # leaves a residual orthogonal to the range of Phi
+    from oracle import dense as D
+    X = W.fibonacci_points(400)
+    Phi = H.sphere_phi(X, 9)  # m = 100 < n: full column rank
+    c0 = W.gaussian_columns(100, 2, 3)
+    assert np.allclose(D.inverse(Phi, Phi @ c0), c0, atol=1e-11)
+    f = Phi @ c0 + W.gaussian_columns(400, 2, 9)
+    c = D.inverse(Phi, f)
+    assert np.abs(Phi.T @ (Phi @ c - f)).max() < 1e-9 * np.abs(Phi.T @ f).max()
+    assert np.linalg.norm(Phi @ c - f) <= np.linalg.norm(Phi @ c0 - f) + 1e-12
