@@ -26,6 +26,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "transforms/s (synthesis + weighted adjoint)"
+# DRAM bytes (read + write) per algorithmic byte of the per-stage kernel, from ncu's
+# dram__bytes_read.sum + dram__bytes_write.sum over every stage launch of one timed step on the
+# 16384-point sphere (the launch shapes the autotuner chose there).  Traffic grows in proportion
+# to the bytes a launch streams (1.002 on the largest 16384-point stages), so a full-size
+# launch's traffic is this ratio times its algorithmic bytes.  None: not captured for the
+# current kernel.
+NCU_DRAM_PER_ALG_BYTE = {
+    "k_rowdot synthesis (transfer levels 0..L)": 1.0018,
+    "k_rowdot adjoint (transfer levels L..0)": 1.0042,
+}
 WORKLOADS = {
     # name: (n, lmax, leaf, eps)
     "sphere65536": (65536, 255, 128, 1e-6),
@@ -306,10 +316,12 @@ def run_ours(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = (kbytes / 1e9) / (kms / 1e3) if kms > 0 else 0.0
+    ratio = NCU_DRAM_PER_ALG_BYTE.get(name)
+    traffic = ratio * kbytes / max(kl, 1) if ratio else None  # bytes per launch, like achieved
     step_bytes = 2 * all_bytes  # one synthesis + one adjoint (factor bytes dominate)
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else
-                "fallback 6800 GB/s", "traffic": None, "launches": int(kl), "avg_launch_ms": kms / max(kl, 1),
+                "fallback 6800 GB/s", "traffic": traffic, "launches": int(kl), "avg_launch_ms": kms / max(kl, 1),
                 "step_algorithmic_GB": step_bytes / 1e9,
                 "step_frac": (step_bytes / 1e9) / (ms_step / 1e3) / peak}
     per_stage = {"path": args.path, "launches_per_step": int((syn_n.sum() + adj_n.sum()) // K),

@@ -844,8 +844,8 @@ int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t 
     return synth_stages<R, C>(c, cin, ldc, f, ldf, wt, [&](int dir, int s) { return stage_cfg(c, dir, s, rt); },
                               scale);
   }
-  if (!use_tc(c) && (c.d.path == 2 || c.d.tune_nrhs != c.nrhs))
-    if (const int rt = fused_rt(c, 0)) {
+  if (!use_tc(c))
+    if (const int rt = fused_rt(c, 0)) {  // only when the persistent path is selected
       const int rc = fused_dispatch<R, C, 0>(c, rt, cin, ldc, f, ldf, wt);
       if (rc >= 0) return rc;
     }
@@ -858,8 +858,8 @@ int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t 
 }
 template <class R, bool C>
 int adjoint_dispatch(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t ldc, bool wt) {
-  if (!use_tc(c) && (c.d.path == 2 || c.d.tune_nrhs != c.nrhs))
-    if (const int rt = fused_rt(c, 1)) {
+  if (!use_tc(c))
+    if (const int rt = fused_rt(c, 1)) {  // only when the persistent path is selected
       const int rc = fused_dispatch<R, C, 1>(c, rt, f, ldf, cout, ldc, wt);
       if (rc >= 0) return rc;
     }

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BatchParams p) {
     if (t < 0) break;
     const MhtBItem bi = p.items[t];
     const MhtBatchRec& r = p.recs[bi.rec];
-    const int mode = r.mode, cplx = r.cplx, rt = rec_rt(r), wait_ctr = r.wait_ctr, done_ctr = r.done_ctr;
+    const int cplx = r.cplx, rt = rec_rt(r), wait_ctr = r.wait_ctr, done_ctr = r.done_ctr;
     const MhtItem it{bi.blk, bi.start, bi.count_sib & 0x7fffffff, int(unsigned(bi.count_sib) >> 31)};
     const MhtBlockDesc d = reinterpret_cast<const MhtBlockDesc*>(r.desc)[bi.blk];
     if (threadIdx.x == 0 && wait_ctr >= 0 && !wait_count(p.done + wait_ctr, r.wait_count, p.abort)) {
@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(kThreads) k_batch(BatchParams p) {
       ok = false;
       break;
     }
-    (void)mode;
     if (cplx)
       ok = rt == 1 ? batch_item<true, 1>(r, it, d, sm, cons, p.status, p.use_wts, prod)
                    : batch_item<true, 8>(r, it, d, sm, cons, p.status, p.use_wts, prod);

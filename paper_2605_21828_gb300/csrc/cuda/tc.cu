@@ -119,6 +119,11 @@ __device__ __forceinline__ void cp_async_wait() {
 // core-matrix byte offset of element group (row m, 4-column group c4) in a no-swizzle K-major
 // tile with 32 columns: 8 x 16-byte core matrices, 128 bytes apart along K, 1024 along M/N
 __device__ __forceinline__ int core_off(int m, int c4) { return (m >> 3) * 1024 + c4 * 128 + (m & 7) * 16; }
+// A element group q (0..1023) of a 128 x 32 chunk: 8 consecutive q are the 8 rows of one core
+// matrix (their 16-byte stores fill 128 contiguous bytes: no bank conflicts), and a warp's 32
+// groups read 64 contiguous bytes from each of 8 rows
+__device__ __forceinline__ int a_row(int q) { return (q >> 6) * 8 + (q & 7); }
+__device__ __forceinline__ int a_col4(int q) { return (q >> 3) & 7; }
 
 // C: complex factors and vectors.  The complex product y = A x is computed as one real
 // product: A's interleaved storage is a real matrix of 2K columns, and column n of B holds
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
 #pragma unroll
       for (int u = 0; u < A_BYTES / 16 / kTcThreads; ++u) {
         const int q = tid + kTcThreads * u;
-        const int m = q >> 3, c4 = q & 7, kr = x * kTcK + c4 * 4;
+        const int m = a_row(q), c4 = a_col4(q), kr = x * kTcK + c4 * 4;
         const bool ok = m < it.count && kr < ldr;
         const float* src = ok ? p.data + (d.t_off + (long long)(it.start + m) * d.ldt) * W + kr : p.data;
         cp_async16(rs + q * 16, src, ok ? 16u : 0u);
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
       split(v.y, h.y, l.y);
       split(v.z, h.z, l.z);
       split(v.w, h.w, l.w);
-      const int off = core_off(q >> 3, q & 7);
+      const int off = core_off(a_row(q), a_col4(q));
       *reinterpret_cast<float4*>(Ahi + off) = h;
       *reinterpret_cast<float4*>(Alo + off) = l;
     }
