@@ -558,6 +558,31 @@ def run_batch(args):
     peak = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock, TFLOP/s
     achieved = flops / 1e12 / (ms / 1e3)
     factor_bytes = sum(2 * sum(p.level_info(s)["algorithmic_bytes"] for s in range(p.levels + 2)) for p in plans)
+
+    # the tensor-core form: every instance's own apply (3xTF32 block products from 16 RHS on) on
+    # forked streams, replayed from one CUDA graph; its difference from the FP32 results
+    bt.set_mode("3xtf32")
+    for i in range(len(plans)):
+        bt.c[i].copy_(cin[i])
+    for _ in range(Wm):
+        step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_tc = e0.elapsed_time(e1) / K
+    for i in range(len(plans)):
+        bt.c[i].copy_(cin[i])
+    f_tc = bt.synthesize()
+    torch.cuda.synchronize()
+    diff = max(float(torch.linalg.norm((f_tc[i] - f_batch[i]).to(torch.complex128 if plans[i].complex else
+                                                                   torch.float64)) /
+                     torch.linalg.norm(f_batch[i].to(torch.complex128 if plans[i].complex else torch.float64)))
+               for i in range(len(plans)))
+    status_tc = bt.check()
+    bt.set_mode("fp32")
     info = bt.info()
     line = {"metric": "transforms/s (synthesis + weighted adjoint), batched ragged", "value": total_rhs / (ms / 1e3),
             "unit": "transforms/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms,
@@ -574,6 +599,11 @@ def run_batch(args):
                                   "launches_per_step": 2 * sum(p.levels + 2 for p in plans),
                                   "identical_results": bool(same)},
             "speedup_vs_per_instance": ms_plain / ms,
+            "tensor_core_form": {"ms_per_step": ms_tc, "transforms_per_s": total_rhs / (ms_tc / 1e3),
+                                 "speedup_vs_per_instance_fp32": ms_plain / ms_tc,
+                                 "max_rel_diff_synthesis_vs_fp32_form": diff, "device_status": status_tc,
+                                 "kernels": "k_tc3 (instances with >= 16 real / 8 complex RHS) and k_rowdot, "
+                                            "8 forked streams in one CUDA graph"},
             "roofline": {"bound": "alu", "kernel": "k_batch (both directions, all instances)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",

@@ -383,6 +383,11 @@ mht_status mht_batch_set_io(mht_batch* batch, void* const* c_dev, const int64_t*
 mht_status mht_batch_synthesize(mht_batch* batch, void* stream);
 /* c_i = Phi_i^H W_i f_i (weighted != 0) or Phi_i^H f_i for every instance. */
 mht_status mht_batch_analyze(mht_batch* batch, int32_t weighted, void* stream);
+/* MHT_APPLY_FP32 (default): the persistent FP32 kernel above.  MHT_APPLY_3XTF32: every
+ * instance runs its own per-stage apply (tcgen05 3xTF32 block products from 16 real / 8 complex
+ * RHS on, FP32 kernels below that) on eight forked streams, all captured once into one CUDA graph
+ * and replayed; results equal mht_synthesize / mht_analyze of each plan in MHT_APPLY_3XTF32. */
+mht_status mht_batch_set_mode(mht_batch* batch, mht_apply_mode mode);
 /* 1 (default): launches replay CUDA graphs; 0: plain stream launches (same work). */
 mht_status mht_batch_set_graph(mht_batch* batch, int32_t use_graph);
 /* Work items per direction and CTAs of one persistent launch (needs a current device). */

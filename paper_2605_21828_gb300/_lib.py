@@ -106,6 +106,7 @@ SIGNATURES = {
     "mht_batch_synthesize": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mht_batch_analyze": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "mht_batch_set_graph": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mht_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "mht_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "mht_batch_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "mht_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),

@@ -526,6 +526,12 @@ class Batch:
         L.check(L.load().mht_batch_autotune(self._h, self._stream(), C.byref(ms)))
         return ms.value
 
+    def set_mode(self, mode: str = "fp32"):
+        """'fp32': one persistent FP32 launch per direction; '3xtf32': a CUDA graph of each
+        instance's own apply with tensor-core block products for wide RHS counts."""
+        L.check(L.load().mht_batch_set_mode(self._h, _MODES[mode]))
+        return self
+
     def set_graph(self, use_graph: bool = True):
         L.check(L.load().mht_batch_set_graph(self._h, 1 if use_graph else 0))
         return self

@@ -372,6 +372,77 @@ int batch_autotune(const BatchLaunch& syn, const BatchLaunch& ana, int max_nslot
   return rc;
 }
 
+struct TcGroup {
+  static constexpr int kStreams = 8;
+  cudaStream_t s0 = nullptr;
+  cudaStream_t side[kStreams] = {};
+  cudaEvent_t ev[kStreams + 1] = {};
+  cudaGraphExec_t exec = nullptr;
+};
+
+void tc_group_destroy(TcGroup* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (cudaEvent_t e : g->ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : g->side)
+    if (s) cudaStreamDestroy(s);
+  if (g->s0) cudaStreamDestroy(g->s0);
+  delete g;
+}
+
+int batch_tc_run(mht_batch& B, int dir, bool weighted, void* stream, std::string& err) {
+  TcGroup*& g = B.tc[dir == 0 ? 0 : (weighted ? 2 : 1)];
+  if (!g) {
+    g = new TcGroup();
+    int rc = cuda_check(cudaStreamCreateWithFlags(&g->s0, cudaStreamNonBlocking), err, "stream");
+    for (int k = 0; k < TcGroup::kStreams && !rc; ++k)
+      rc = cuda_check(cudaStreamCreateWithFlags(&g->side[k], cudaStreamNonBlocking), err, "stream");
+    for (int k = 0; k <= TcGroup::kStreams && !rc; ++k)
+      rc = cuda_check(cudaEventCreateWithFlags(&g->ev[k], cudaEventDisableTiming), err, "event");
+    if (!rc) rc = cuda_check(cudaStreamBeginCapture(g->s0, cudaStreamCaptureModeThreadLocal), err, "capture");
+    if (rc) {
+      tc_group_destroy(g);
+      g = nullptr;
+      return rc;
+    }
+    // fork: every side stream starts after the capture origin
+    rc = cuda_check(cudaEventRecord(g->ev[TcGroup::kStreams], g->s0), err, "fork");
+    for (int k = 0; k < TcGroup::kStreams && !rc; ++k)
+      rc = cuda_check(cudaStreamWaitEvent(g->side[k], g->ev[TcGroup::kStreams], 0), err, "fork");
+    for (int i = 0; i < B.n && !rc; ++i) {
+      const BatchInst& I = B.inst[i];
+      DeviceView dv;
+      dv.base = B.image_dev + I.image_off;
+      dv.ws = B.ws_dev + I.ws_off;
+      dv.ws_bytes = I.ws_bytes;
+      dv.max_nrhs = I.nrhs;
+      dv.path = 1;
+      cudaStream_t st = g->side[i % TcGroup::kStreams];
+      void* c = reinterpret_cast<void*>(I.c);
+      void* f = reinterpret_cast<void*>(I.f);
+      rc = dir == 0 ? apply_synthesize(I.shape, I.meta, dv, c, I.ldc, f, I.ldf, I.nrhs, false, MHT_APPLY_3XTF32, st, err)
+                    : apply_analyze(I.shape, I.meta, dv, f, I.ldf, c, I.ldc, I.nrhs, weighted, MHT_APPLY_3XTF32, st, err);
+    }
+    // join: the origin waits for every side stream
+    for (int k = 0; k < TcGroup::kStreams && !rc; ++k) {
+      rc = cuda_check(cudaEventRecord(g->ev[k], g->side[k]), err, "join");
+      if (!rc) rc = cuda_check(cudaStreamWaitEvent(g->s0, g->ev[k], 0), err, "join");
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(g->s0, &graph);
+    if (!rc && e != cudaSuccess) rc = cuda_check(e, err, "capture end");
+    if (!rc) rc = cuda_check(cudaGraphInstantiate(&g->exec, graph, 0), err, "graph instantiate");
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) {
+      tc_group_destroy(g);
+      g = nullptr;
+      return rc;
+    }
+  }
+  return cuda_check(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), err, "graph launch");
+}
+
 int batch_grid_size(const BatchLaunch& b, std::string& err) {
   int grid = 0;
   size_t smem = 0;

@@ -248,9 +248,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
             a = ((long long)src * p.is_e + (long long)(r0 + rn) * p.is_k) * W;
             if (C) a += (n < NR) ? (kl & 1) : 1 - (kl & 1);  // (xr, -xi) / (xi, xr): component
           }
-          cp_async4(rs + A_BYTES + (g * 4 + j) * 4, ok ? p.in0 + a : p.in0, ok ? 4u : 0u);
+          // raw B layout [j][group]: a warp's copies of one j land in consecutive words
+          cp_async4(rs + A_BYTES + (j * BG + g) * 4, ok ? p.in0 + a : p.in0, ok ? 4u : 0u);
           if (NB == 2)
-            cp_async4(rs + A_BYTES + B_BYTES + (g * 4 + j) * 4, (ok && p.in1) ? p.in1 + a : p.in0,
+            cp_async4(rs + A_BYTES + B_BYTES + (j * BG + g) * 4, (ok && p.in1) ? p.in1 + a : p.in0,
                       (ok && p.in1) ? 4u : 0u);
         }
       }
@@ -335,15 +336,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
     const float* kwc = kw + (c % kTcDepth) * kTcK;
     for (int g = tid; g < BG; g += kTcThreads) {
       const int n = g % N, c4 = g / N;
-      float4 v = *reinterpret_cast<const float4*>(rs + A_BYTES + g * 16);
-      if (NB == 2) {
-        const float4 v1 = *reinterpret_cast<const float4*>(rs + A_BYTES + B_BYTES + g * 16);
-        v.x += v1.x;
-        v.y += v1.y;
-        v.z += v1.z;
-        v.w += v1.w;
+      const float* rb = reinterpret_cast<const float*>(rs + A_BYTES);
+      float x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[j] = rb[j * BG + g];
+        if (NB == 2) x[j] += rb[BG * 4 + j * BG + g];  // sibling buffer (B_BYTES = 4 BG floats later)
       }
-      float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         x[j] *= kwc[c4 * 4 + j];

@@ -635,6 +635,15 @@ mht_status mht_batch_bind_device(mht_batch* batch, void* image_dev, size_t image
     std::vector<uint8_t> zero(256, 0);
     if (int rc = mht::device_upload(batch->ws_dev + batch->status_off, zero.data(), 256, stream, err))
       mht::fail(mht_status(rc), err);
+    for (const mht::BatchInst& I : batch->inst) {  // status words of the per-instance workspaces
+      const size_t so = I.meta.status_offset(I.nrhs, I.n, I.m);
+      if (int rc = mht::device_upload(batch->ws_dev + I.ws_off + so, zero.data(), sizeof(unsigned), stream, err))
+        mht::fail(mht_status(rc), err);
+    }
+    for (auto*& g : batch->tc) {
+      mht::tc_group_destroy(g);
+      g = nullptr;
+    }
     for (mht::BatchInst& I : batch->inst) I.plan = nullptr;
     batch->bound = true;
     batch->io_set = false;
@@ -663,6 +672,10 @@ mht_status mht_batch_set_io(mht_batch* batch, void* const* c_dev, const int64_t*
       if (int rc = mht::device_upload(batch->image_dev + batch->recs_off[dir], batch->recs[dir].data(),
                                       batch->recs[dir].size() * sizeof(MhtBatchRec), stream, err))
         mht::fail(mht_status(rc), err);
+    for (auto*& g : batch->tc) {  // captured with the previous vectors
+      mht::tc_group_destroy(g);
+      g = nullptr;
+    }
     batch->io_set = true;
     return MHT_OK;
   });
@@ -673,6 +686,10 @@ mht_status batch_run(mht_batch* batch, int dir, bool weighted, void* stream) {
   if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
   if (!batch->bound || !batch->io_set) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound or has no vectors");
   std::string err;
+  if (batch->mode == MHT_APPLY_3XTF32) {
+    if (int rc = mht::batch_tc_run(*batch, dir, weighted, stream, err)) mht::fail(mht_status(rc), err);
+    return MHT_OK;
+  }
   const mht::BatchLaunch b = mht::batch_launch_desc(*batch, dir, weighted);
   if (!batch->use_graph) {
     if (int rc = mht::batch_launch(b, stream, err)) mht::fail(mht_status(rc), err);
@@ -692,6 +709,15 @@ mht_status mht_batch_synthesize(mht_batch* batch, void* stream) {
 
 mht_status mht_batch_analyze(mht_batch* batch, int32_t weighted, void* stream) {
   return guarded([&]() -> mht_status { return batch_run(batch, 1, weighted != 0, stream); });
+}
+
+mht_status mht_batch_set_mode(mht_batch* batch, mht_apply_mode mode) {
+  return guarded([&]() -> mht_status {
+    if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
+    if (mode != MHT_APPLY_FP32 && mode != MHT_APPLY_3XTF32) mht::fail(MHT_ERR_INVALID_ARG, "FP32 or 3XTF32 only");
+    batch->mode = mode;
+    return MHT_OK;
+  });
 }
 
 mht_status mht_batch_set_graph(mht_batch* batch, int32_t use_graph) {
@@ -724,6 +750,12 @@ mht_status mht_batch_check(mht_batch* batch, void* stream, int32_t* flags) {
     unsigned v = 0;
     std::string err;
     if (int rc = mht::device_status(batch->ws_dev + batch->status_off, stream, &v, err)) mht::fail(mht_status(rc), err);
+    for (const mht::BatchInst& I : batch->inst) {  // the tensor-core form reports per instance
+      unsigned u = 0;
+      const size_t so = I.meta.status_offset(I.nrhs, I.n, I.m);
+      if (int rc = mht::device_status(batch->ws_dev + I.ws_off + so, stream, &u, err)) mht::fail(mht_status(rc), err);
+      v |= u;
+    }
     *flags = int32_t(v);
     if (v) return set_error(MHT_ERR_TIMEOUT, "a bounded wait in the batched apply gave up");
     return MHT_OK;

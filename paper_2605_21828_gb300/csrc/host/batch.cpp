@@ -44,6 +44,30 @@ void batch_init(mht_batch& B, mht_plan* const* plans, int count, const int64_t* 
     I.index_off = p->P.index_off;
     I.perm_off = p->P.perm_off;
     I.weights_off = p->P.weights_off;
+    {  // the packing's layout without its (large) image
+      const Packed& Q = p->P;
+      Packed& M = I.meta;
+      M.fp64 = Q.fp64;
+      M.cplx = Q.cplx;
+      M.elem_bytes = Q.elem_bytes;
+      M.L = Q.L;
+      M.nb = Q.nb;
+      M.data_off = Q.data_off;
+      M.index_off = Q.index_off;
+      M.perm_off = Q.perm_off;
+      M.weights_off = Q.weights_off;
+      M.vecoff_off = Q.vecoff_off;
+      M.st = Q.st;
+      M.fused[0] = Q.fused[0];
+      M.fused[1] = Q.fused[1];
+      M.vec_off = Q.vec_off;
+      M.vec_entries = Q.vec_entries;
+      M.index_entries = Q.index_entries;
+    }
+    I.shape.n = p->F.n;
+    I.shape.m = p->F.m;
+    I.shape.L = p->F.L;
+    I.shape.cplx = p->F.cplx;
     for (int dir = 0; dir < 2; ++dir) {
       I.desc_off[dir].resize(I.L + 2);
       for (int s = 0; s < I.L + 2; ++s) I.desc_off[dir][s] = p->P.st[s].dir[dir].desc_off;
@@ -118,7 +142,10 @@ void batch_init(mht_batch& B, mht_plan* const* plans, int count, const int64_t* 
   for (BatchInst& I : B.inst) {
     I.ws_off = ws;
     I.region_bytes = align256(size_t(std::max<int64_t>(I.vec_off.back(), 1)) * I.nrhs * I.es);
-    ws += 3 * I.region_bytes;
+    // a full per-plan workspace (its first three regions are the level vectors the persistent
+    // kernel uses), so that the tensor-core form can run each instance's own apply in place
+    I.ws_bytes = align256(I.meta.workspace_bytes(I.nrhs, I.n, I.m));
+    ws += I.ws_bytes;
   }
   B.counters_off = ws;
   B.nctr = nctr;
@@ -202,6 +229,10 @@ BatchLaunch batch_launch_desc(const mht_batch& B, int dir, bool weighted) {
 mht_batch::~mht_batch() {
   for (auto*& g : graphs) {
     mht::batch_graph_destroy(g);
+    g = nullptr;
+  }
+  for (auto*& g : tc) {
+    mht::tc_group_destroy(g);
     g = nullptr;
   }
 }

@@ -281,10 +281,14 @@ struct BatchInst {
   size_t image_off = 0, image_bytes = 0, data_off = 0, index_off = 0, perm_off = 0, weights_off = 0;
   std::vector<size_t> desc_off[2];  // per stage, relative to the instance image
   int rec_base[2] = {0, 0}, ctr_base[2] = {0, 0};
-  size_t ws_off = 0, region_bytes = 0;
+  size_t ws_off = 0, region_bytes = 0, ws_bytes = 0;  // a full per-plan workspace each
   uint64_t c = 0, f = 0;            // caller vectors (set_io)
   int64_t ldc = 0, ldf = 0;
+  Packed meta;                      // the plan's packing without its image (per-plan applies)
+  Factorization shape;              // n, m, L only
 };
+struct TcGroup;                      // CUDA graph of per-instance applies (tensor-core form)
+void tc_group_destroy(TcGroup* g);
 }  // namespace mht
 
 struct mht_batch {
@@ -301,7 +305,9 @@ struct mht_batch {
   uint8_t* ws_dev = nullptr;
   bool bound = false, io_set = false;
   int use_graph = 1;
+  mht_apply_mode mode = MHT_APPLY_FP32;  // 3XTF32: graph of per-instance tensor-core applies
   mht::BatchGraph* graphs[3] = {nullptr, nullptr, nullptr};  // synthesis, analysis, weighted
+  mht::TcGroup* tc[3] = {nullptr, nullptr, nullptr};
   ~mht_batch();
 };
 
@@ -309,4 +315,7 @@ namespace mht {
 void batch_init(mht_batch& B, mht_plan* const* plans, int count, const int64_t* nrhs);
 void batch_fill_records(mht_batch& B);
 BatchLaunch batch_launch_desc(const mht_batch& B, int dir, bool weighted);
+// Tensor-core form of a batch: every instance's own per-stage apply (3xTF32 products from 16
+// real / 8 complex RHS) on 8 forked streams, captured once into a CUDA graph and replayed.
+int batch_tc_run(mht_batch& B, int dir, bool weighted, void* stream, std::string& err);
 }  // namespace mht

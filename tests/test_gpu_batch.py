@@ -138,3 +138,38 @@ def test_batch_autotune_keeps_results(torch_cuda):
     for i, (F, _, k) in enumerate(inst):
         assert torch.equal(before[i], after[i])  # launch shape does not change the arithmetic
         assert _rel(after[i].cpu().numpy(), B.synthesize(F, Cs[i])) <= 1e-6
+
+
+def test_batch_tensor_core_form_matches_per_plan_apply(torch_cuda):
+    # 3xTF32 form: each instance's own apply (tensor cores from 16 real / 8 complex RHS) on
+    # forked streams inside one CUDA graph; equal bit for bit to the per-plan 3xTF32 apply
+    from paper_2605_21828_gb300 import Batch, Plan
+    torch = torch_cuda
+    inst = _inst()
+    ks = [20, 9, 1, 17, 2, 16]  # wide tiles on the tensor cores, narrow ones on SIMT
+    rng = np.random.default_rng(12)
+    weights = [w if w is not None else rng.uniform(0.5, 1.5, F.n) for F, w, _ in inst]
+    plans = [Plan.from_factors(oracle_to_arrays(F), mode="3xtf32", weights=w)
+             for (F, _, _), w in zip(inst, weights)]
+    bt = Batch(plans, ks).bind().set_mode("3xtf32")
+    Cs = [W.gaussian_columns(F.m, k, 130 + i, complex_=F.complex_) for i, ((F, _, _), k) in enumerate(zip(inst, ks))]
+    Gs = [W.gaussian_columns(F.n, k, 150 + i, complex_=F.complex_) for i, ((F, _, _), k) in enumerate(zip(inst, ks))]
+    for i in range(len(inst)):
+        bt.c[i].copy_(torch.from_numpy(Cs[i]).to(bt.c[i].dtype))
+        bt.f[i].copy_(torch.from_numpy(Gs[i]).to(bt.f[i].dtype))
+    cs = [c.clone() for c in bt.analyze(weighted=True)]
+    for i in range(len(inst)):
+        bt.c[i].copy_(torch.from_numpy(Cs[i]).to(bt.c[i].dtype))
+    fs = [f.clone() for f in bt.synthesize()]
+    assert bt.check() == 0
+    for i, ((F, _, _), k) in enumerate(zip(inst, ks)):
+        assert _rel(fs[i].cpu().numpy(), B.synthesize(F, Cs[i])) <= 1e-6, i
+        assert _rel(cs[i].cpu().numpy(), B.analyze(F, Gs[i], weights[i])) <= 1e-6, i
+        p = plans[i].bind(max_nrhs=k).set_path("staged")
+        dt = bt.c[i].dtype
+        assert torch.equal(p.synthesize_raw(torch.from_numpy(Cs[i]).to(dt).cuda()), fs[i]), i
+        assert torch.equal(p.analyze_raw(torch.from_numpy(Gs[i]).to(dt).cuda(), weighted=True), cs[i]), i
+    # the graph replays: a second synthesis gives the same vectors
+    f2 = bt.synthesize()
+    for a, b in zip(fs, f2):
+        assert torch.equal(a, b)
