@@ -33,8 +33,8 @@ METRIC = "transforms/s (synthesis + weighted adjoint)"
 # launch's traffic is this ratio times its algorithmic bytes.  None: not captured for the
 # current kernel.
 NCU_DRAM_PER_ALG_BYTE = {
-    "k_rowdot synthesis (transfer levels 0..L)": 1.0018,
-    "k_rowdot adjoint (transfer levels L..0)": 1.0042,
+    "k_rowdot synthesis (transfer levels 0..L)": 1.0006,
+    "k_rowdot adjoint (transfer levels L..0)": 1.0033,
 }
 WORKLOADS = {
     # name: (n, lmax, leaf, eps)

@@ -19,6 +19,9 @@ namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr size_t kTileBytes = 512 * 1024;   // target matrix bytes per per-stage work item
+constexpr size_t kMinTileBytes = 32 * 1024; // smallest target (stages with little data)
+constexpr size_t kResidentCtas = 608;       // 4 CTAs on each of 152 SMs
+constexpr size_t kItemsPerCta = 4;
 constexpr int kItemRows = 512;               // and at most this many rows
 constexpr size_t kPItemBytes = 256 * 1024;  // largest persistent work item
 constexpr int kPItemRows = 1024;             // and at most this many rows (staged per item)
@@ -145,18 +148,21 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
     }
   }
 
-  // work items: row ranges of about kTileBytes
+  // work items: row ranges of about kTileBytes, smaller in stages too small to give every
+  // resident CTA of a persistent launch (about kResidentCtas) several items to stream
   std::vector<std::vector<MhtItem>> items[2];
   items[0].assign(nst, {});
   items[1].assign(nst, {});
   for (int dir = 0; dir < 2; ++dir)
     for (int s = 0; s < nst; ++s) {
       StageDir& D = P.st[s].dir[dir];
+      const size_t stage_bytes = size_t(P.st[s].t_entries) * es;
+      const size_t tile = std::max(kMinTileBytes, std::min(kTileBytes, stage_bytes / (kItemsPerCta * kResidentCtas)));
       for (int64_t b = 0; b < nb; ++b) {
         const MhtBlockDesc& d = desc[dir][s][b];
         const int sib = (dir == 1 && s >= 1 && s <= L) ? int((b >> (L - s)) & 1) : 0;
         const size_t rowbytes = size_t(d.ldt) * es;
-        const int rpi = int(std::min<size_t>(kItemRows, std::max<size_t>(1, rowbytes ? kTileBytes / rowbytes
+        const int rpi = int(std::min<size_t>(kItemRows, std::max<size_t>(1, rowbytes ? tile / rowbytes
                                                                                        : size_t(kItemRows))));
         if (d.rows == 0) {
           // adjoint of an ID block without T~ (full rank): still copies the skeleton out
