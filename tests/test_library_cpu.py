@@ -285,3 +285,35 @@ def test_batch_create_validates_and_counts_items(mht_lib):
     st = lib.mht_batch_synthesize(bt._h, None)
     assert st == 9  # not bound
     bt.close()
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(mht_lib):
+    import ctypes as C
+    from paper_2605_21828_gb300 import _lib
+    lib = _lib.load()
+    X, Phi, lam = _sphere(256, 15)
+    p = _plan_cls().build(n=256, m=256, eigenvalues=lam, evaluator="sphere", points=X, eps=1e-6, leaf_size=32)
+    dummy = C.c_void_p(256)
+    # unbound plans: every device entry point refuses before touching the GPU
+    assert lib.mht_plan_autotune(p._h, 1, None) == 9
+    assert lib.mht_filter(p._h, dummy, 256, C.c_void_p(512), 256, 1, dummy, 1, None) == 9
+    assert lib.mht_synthesize_scaled(p._h, dummy, 256, dummy, C.c_void_p(512), 256, 1, None) == 9
+    it, rr = C.c_int32(), C.c_double()
+    assert lib.mht_inverse_lsqr(p._h, dummy, 256, C.c_void_p(512), 256, 1, dummy, 1 << 20, 10, 1e-6, None,
+                                C.byref(it), C.byref(rr)) == 9
+    nb = C.c_size_t()
+    assert lib.mht_lsqr_scratch_bytes(p._h, 2, C.byref(nb)) == 0 and nb.value > 2 * 256 * 4
+    assert lib.mht_lsqr_scratch_bytes(p._h, 0, C.byref(nb)) == 1
+    cfg = (C.c_int32 * 5)()
+    assert lib.mht_plan_tune_info(p._h, 0, 0, cfg, None) == 1  # not tuned
+    assert lib.mht_plan_set_path(p._h, 3) == 1
+    # batches: mode and graph switches, unbound launches
+    h = C.c_void_p()
+    arr = (C.c_void_p * 1)(p._h)
+    ks = (C.c_int64 * 1)(2)
+    assert lib.mht_batch_create(arr, 1, ks, C.byref(h)) == 0
+    assert lib.mht_batch_set_mode(h, 0) == 1  # FP64 is not a batch mode
+    assert lib.mht_batch_set_mode(h, 2) == 0
+    assert lib.mht_batch_analyze(h, 1, None) == 9
+    assert lib.mht_batch_autotune(h, None, None) == 9
+    assert lib.mht_batch_destroy(h) == 0
