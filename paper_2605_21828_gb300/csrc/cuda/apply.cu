@@ -11,12 +11,15 @@
 // HBM bandwidth.  The packed plan holds every matrix in both orientations, so both
 // directions are "rows times a gathered vector":
 //   * k_rowdot: one persistent launch per stage; each CTA takes work items (block, row range
-//     of ~128 KB) in a fixed stride, and thread 0 keeps a ring of 32 KB shared-memory slots
-//     filled by 1-D TMA bulk copies (cp.async.bulk, completion on mbarriers) across item
-//     boundaries, while all threads gather the block's input vector from L2;
+//     of up to 512 KB, less in small stages) in a fixed stride, and thread 0 keeps a ring of
+//     shared-memory slots (size and depth autotuned) filled by 1-D TMA bulk copies
+//     (cp.async.bulk, completion on mbarriers) across item boundaries, while all threads
+//     gather the block's input vector from L2;
 //   * each warp then reduces whole rows from shared memory with 128-bit loads, compensated
 //     FP32 sums and warp shuffles (building blocks in rowdot.cuh);
-//   * k_fused: one persistent launch for all stages with per-block completion counters.
+//   * k_fused: one persistent launch for all stages with per-block completion counters
+//     (selected explicitly; also the engine of the allocation-free synthesis);
+//   * this file also holds the per-stage dispatch, the autotuner and the spectral filter graph.
 // The adjoint is a gather: the sibling blocks (2p, nu), (2p+1, nu) that share an input pair
 // write separate buffers and the next stage sums them while loading -- no atomics, so the
 // result is deterministic.  Every mbarrier wait is bounded; on timeout the kernel sets a bit
