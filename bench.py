@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--multi-rhs", type=int, default=64, help="extra measurement at this many RHS (0: off)")
-    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64"],
+    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64", "torus_sweep"],
                     help="batch64: 64 ragged instances (torus / sphere / deformed sphere, n in [2000, 40000], "
-                         "m = n/4, 1-128 RHS each) in one persistent launch per direction")
+                         "m = n/4, 1-128 RHS each) in one persistent launch per direction; torus_sweep: the flat-torus "
+                         "memory law (m = ceil(n/25), eps 1e-3 and 1e-6) with single-RHS apply times")
     ap.add_argument("--plan-cache", default=os.environ.get("MHT_PLAN_CACHE", ""))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -615,12 +616,72 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_torus_sweep(args):
+    """Flat torus, m = ceil(n/25) lowest modes, eps in {1e-3, 1e-6}, leaf 64 (the memory-scaling
+    experiment of Sec. 6.1): stored entries, compression against dense Phi, and the FP32
+    single-RHS synthesis + analysis time of each plan."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2605_21828_gb300 import Plan
+    from paper_2605_21828_gb300.build import build_library
+    build_library()
+    dev = torch.device("cuda", 0)
+    sizes = [int(x) for x in os.environ.get("MHT_SWEEP_SIZES", "4096,16384,65536,262144").split(",")]
+    points = []
+    for eps in (1e-3, 1e-6):
+        for n in sizes:
+            m = -(-n // 25)
+            K = W.torus_modes_lowest(m)
+            t0 = time.time()
+            p = Plan.build(n=n, m=m, eigenvalues=W.torus_eigenvalues(K), evaluator="torus",
+                           points=W.torus_points(n), torus_modes=K, eps=eps, leaf_size=64, mode="fp32")
+            build_s = time.time() - t0
+            p.bind(device=dev, max_nrhs=1)
+            p.autotune(1)
+            c = torch.from_numpy(W.gaussian(m, 1, True)).to(torch.complex64).to(dev)
+            for _ in range(3):
+                p.analyze_raw(p.synthesize_raw(c), weighted=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 50
+            e0.record()
+            for _ in range(reps):
+                p.analyze_raw(p.synthesize_raw(c), weighted=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            info = p.info()
+            alg = 2 * sum(p.level_info(s_)["algorithmic_bytes"] for s_ in range(p.levels + 2))
+            points.append({"eps": eps, "n": n, "m": m, "levels": p.levels, "stored_entries": info["stored_entries"],
+                           "compression_vs_dense": n * m / info["stored_entries"], "build_s": round(build_s, 1),
+                           "ms_per_step": ms, "GBps_algorithmic": alg / 1e9 / (ms / 1e3)})
+            p.close()
+            del p
+            torch.cuda.empty_cache()
+    fit = {}
+    for eps in (1e-3, 1e-6):
+        pts = [q for q in points if q["eps"] == eps]
+        if len(pts) >= 2:
+            x = np.log([q["n"] for q in pts])
+            fit[str(eps)] = {"stored_exponent": float(np.polyfit(x, np.log([q["stored_entries"] for q in pts]), 1)[0]),
+                             "time_exponent": float(np.polyfit(x, np.log([q["ms_per_step"] for q in pts]), 1)[0])}
+    print(json.dumps({"metric": "flat-torus memory law and apply time (synthesis + adjoint, complex64, 1 RHS)",
+                      "unit": "ms per step", "n_gpus": 1, "data": "synthetic", "dtype": "c64",
+                      "config": {"workload": "flat torus, uniform points in [-pi,pi]^2, m = ceil(n/25) lowest modes, "
+                                             "leaf 64"},
+                      "points": points, "loglog_fit": fit}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "torus_sweep":
+        run_torus_sweep(args)
     else:
         run_ours(args)
 
