@@ -401,6 +401,13 @@ mht_status mht_batch_check(mht_batch* batch, void* stream, int32_t* flags);
  * graphs are rebuilt).  Overwrites the batch's f and c vectors; synchronizes `stream`;
  * *best_ms (optional) receives the time of the chosen pair for both directions. */
 mht_status mht_batch_autotune(mht_batch* batch, void* stream, double* best_ms);
+/* Testing aid for the failure path of the batched FP32 kernel: makes the dependency of one
+ * phase (1..L+1) of one instance impossible to satisfy on the device, so that the next launch
+ * of that direction gives up its bounded wait (2 s), stops every CTA through the abort word and
+ * reports MHT_ERR_TIMEOUT (flag 2) through mht_batch_check, leaving the context usable.
+ * mht_batch_set_io restores the records.  Synchronous on `stream`. */
+mht_status mht_batch_debug_hold(mht_batch* batch, int32_t direction, int32_t instance, int32_t phase,
+                                void* stream);
 mht_status mht_batch_destroy(mht_batch* batch);
 
 /* ---- persistence and lifetime -------------------------------------------------------- */

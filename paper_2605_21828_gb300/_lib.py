@@ -110,6 +110,7 @@ SIGNATURES = {
     "mht_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "mht_batch_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "mht_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "mht_batch_debug_hold": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "mht_batch_destroy": (C.c_int, [C.c_void_p]),
     "mht_plan_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mht_plan_load": (C.c_int, [C.c_char_p, C.POINTER(Options), C.POINTER(C.c_void_p)]),

@@ -501,9 +501,16 @@ class Batch:
         ldc = (C.c_int64 * nb)(*[m for (_, m, _) in self.shapes])
         ldf = (C.c_int64 * nb)(*[n for (n, _, _) in self.shapes])
         L.check(lib.mht_batch_set_io(self._h, cp, ldc, fp, ldf, stream))
+        self._io = (cp, ldc, fp, ldf)
         self._dev = (img, ws, cs, fs)
         self.c = [t.t() for t in cs]  # m x k views of the column-major buffers
         self.f = [t.t() for t in fs]
+        return self
+
+    def reset_io(self):
+        """Rewrites the device records of the batch's vectors (undoes a debug hold)."""
+        cp, ldc, fp, ldf = self._io
+        L.check(L.load().mht_batch_set_io(self._h, cp, ldc, fp, ldf, self._stream()))
         return self
 
     def _stream(self):

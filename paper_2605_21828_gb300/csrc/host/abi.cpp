@@ -784,6 +784,25 @@ mht_status mht_batch_autotune(mht_batch* batch, void* stream, double* best_ms) {
   });
 }
 
+mht_status mht_batch_debug_hold(mht_batch* batch, int32_t direction, int32_t instance, int32_t phase, void* stream) {
+  return guarded([&]() -> mht_status {
+    if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
+    if (!batch->bound || !batch->io_set) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound or has no vectors");
+    if (direction < 0 || direction > 1 || instance < 0 || instance >= batch->n)
+      mht::fail(MHT_ERR_INVALID_ARG, "bad direction or instance");
+    const mht::BatchInst& I = batch->inst[instance];
+    if (phase < 1 || phase >= I.L + 2) mht::fail(MHT_ERR_INVALID_ARG, "phase must have a predecessor");
+    const int rec = I.rec_base[direction] + phase;
+    MhtBatchRec r = batch->recs[direction][rec];
+    r.wait_count = 0xffffffffu;  // more completions than the previous phase has items
+    std::string err;
+    if (int rc = mht::device_upload(batch->image_dev + batch->recs_off[direction] + size_t(rec) * sizeof(MhtBatchRec), &r,
+                                    sizeof r, stream, err))
+      mht::fail(mht_status(rc), err);
+    return MHT_OK;
+  });
+}
+
 mht_status mht_batch_destroy(mht_batch* batch) {
   delete batch;
   return MHT_OK;

@@ -173,3 +173,28 @@ def test_batch_tensor_core_form_matches_per_plan_apply(torch_cuda):
     f2 = bt.synthesize()
     for a, b in zip(fs, f2):
         assert torch.equal(a, b)
+
+
+def test_batch_dependency_timeout_is_reported_and_the_context_recovers(torch_cuda):
+    # failure path without a fault: one phase's dependency is made unsatisfiable on the device;
+    # the persistent kernel gives up its bounded wait (2 s), stops every CTA and reports
+    # TIMEOUT; after the records are restored the same batch computes correct results again
+    import ctypes as C
+    from paper_2605_21828_gb300 import Batch, MhtError, Plan, _lib
+    torch = torch_cuda
+    inst = _inst()[:2]
+    plans = [Plan.from_factors(oracle_to_arrays(F), mode="fp32") for F, _, _ in inst]
+    bt = Batch(plans, [k for _, _, k in inst]).bind()
+    Cs = [W.gaussian_columns(F.m, k, 170 + i, complex_=F.complex_) for i, (F, _, k) in enumerate(inst)]
+    for i in range(len(inst)):
+        bt.c[i].copy_(torch.from_numpy(Cs[i]).to(bt.c[i].dtype))
+    lib = _lib.load()
+    _lib.check(lib.mht_batch_debug_hold(bt._h, 0, 0, 2, C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    bt.synthesize()
+    with pytest.raises(MhtError, match="TIMEOUT"):
+        bt.check()
+    bt.reset_io()
+    f = [x.clone() for x in bt.synthesize()]
+    assert bt.check() == 0
+    for i, (F, _, k) in enumerate(inst):
+        assert _rel(f[i].cpu().numpy(), B.synthesize(F, Cs[i])) <= 1e-6

@@ -316,4 +316,5 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(mht_lib):
     assert lib.mht_batch_set_mode(h, 2) == 0
     assert lib.mht_batch_analyze(h, 1, None) == 9
     assert lib.mht_batch_autotune(h, None, None) == 9
+    assert lib.mht_batch_debug_hold(h, 0, 0, 1, None) == 9
     assert lib.mht_batch_destroy(h) == 0
