@@ -301,12 +301,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
     drained = j + 1;
   };
 
-  // prologue: sources and requests of chunks 0 and 1
-  for (int x = 0; x < kTcDepth - 1; ++x) {
-    if (warp == 0 && x < nchunks) sources(x);
-    __syncthreads();
-    request(x);
-  }
+  // prologue: sources of chunks 0..2, requests of chunks 0 and 1.  Afterwards the sources of
+  // chunk c+3 are written during iteration c ahead of drain(c-1)'s barrier, which publishes
+  // them before request(c+3) in the next iteration (two CTA barriers per chunk).
+  if (warp == 0)
+    for (int x = 0; x < kTcDepth && x < nchunks; ++x) sources(x);
+  __syncthreads();
+  for (int x = 0; x < kTcDepth - 1; ++x) request(x);
   for (int c = 0; c < nchunks; ++c) {
     const int s = c & 1;  // stage and TMEM buffer; chunk c-2 used them and was drained already
     unsigned char* st = stages + s * STAGE;
@@ -314,9 +315,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
     unsigned char* Alo = st + A_BYTES;
     unsigned char* Bhi = st + 2 * A_BYTES;
     unsigned char* Blo = st + 2 * A_BYTES + B_BYTES;
-    if (warp == 0 && c + kTcDepth - 1 < nchunks) sources(c + kTcDepth - 1);
-    __syncthreads();
-    if (!*flag) break;
     request(c + kTcDepth - 1);
     cp_async_wait<kTcDepth - 1>();  // this thread's copies of chunk c have landed
     const unsigned char* rs = raw + (c % kTcDepth) * RAW;
@@ -377,7 +375,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
                    : "memory");
     }
     issued = c + 1;
-    if (c >= 1) drain(c - 1);  // overlaps the MMAs of chunk c
+    // sources of chunk c+3 into ring slot c % 3 (chunk c's weights were read before the last
+    // barrier, its requests long before)
+    if (warp == 0 && c + kTcDepth < nchunks) sources(c + kTcDepth);
+    if (c >= 1) drain(c - 1);  // overlaps the MMAs of chunk c; its barrier publishes the sources
+    else __syncthreads();
+    if (!*flag) break;
   }
   cp_async_wait<0>();  // no copy may still target shared memory when the CTA exits
   if (issued > drained) drain(issued - 1);
