@@ -214,6 +214,64 @@ __device__ __forceinline__ void row_dot(const R* __restrict__ row, const R* __re
     }
 }
 
+// Two rows of a real block at once for RT >= 2 RHS (one Kahan chain per RHS, as in row_dot):
+// the staged inputs are loaded once for both rows, halving the shared-memory traffic per
+// multiply-add; each row's arithmetic is exactly row_dot's, so results are identical.
+template <class R, int RT>
+__device__ __forceinline__ void row_dot2(const R* __restrict__ rowa, const R* __restrict__ rowb,
+                                         const R* __restrict__ xs, int ldx, int nvec, int lane, R (&acca)[RT][1],
+                                         R (&accb)[RT][1]) {
+  static_assert(RT >= 2, "pairs of rows are for RHS tiles");
+  constexpr int NS = 16 / sizeof(R);
+  R sa[RT], ca[RT], sb[RT], cb[RT];
+#pragma unroll
+  for (int t = 0; t < RT; ++t) sa[t] = ca[t] = sb[t] = cb[t] = R(0);
+  for (int v = lane; v < nvec; v += 32) {
+    const Vec16<R> ta = *reinterpret_cast<const Vec16<R>*>(rowa + v * NS);
+    const Vec16<R> tb = *reinterpret_cast<const Vec16<R>*>(rowb + v * NS);
+#pragma unroll
+    for (int t = 0; t < RT; ++t) {
+      const Vec16<R> xv = *reinterpret_cast<const Vec16<R>*>(xs + t * ldx + v * NS);
+      R pa[1], pb[1];
+      vec_partial<R, false>(ta, xv, pa);
+      vec_partial<R, false>(tb, xv, pb);
+      if (sizeof(R) == 4) {
+        kahan_add(sa[t], ca[t], pa[0]);
+        kahan_add(sb[t], cb[t], pb[0]);
+      } else {
+        sa[t] += pa[0];
+        sb[t] += pb[0];
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RT; ++t) {
+    if (sizeof(R) == 4) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        R sum = h ? sb[t] : sa[t], err = h ? -cb[t] : -ca[t];
+        // same combination as row_dot with a single chain: TwoSum against a zero second chain
+        R s2, e2;
+        two_sum(sum, R(0), s2, e2);
+        sum = s2;
+        err = e2 + err;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const R so = __shfl_xor_sync(0xffffffffu, sum, o);
+          const R eo = __shfl_xor_sync(0xffffffffu, err, o);
+          two_sum(sum, so, s2, e2);
+          sum = s2;
+          err = err + eo + e2;
+        }
+        (h ? accb : acca)[t][0] = sum + err;
+      }
+    } else {
+      acca[t][0] = warp_sum(sa[t]);
+      accb[t][0] = warp_sum(sb[t]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // out[o(i)] = ident(i) + sum_j M[i, j] x[j] for the rows i of one work item.
 //   SYN_ID: M = T~ (r x K'),           x[j] = in[idx[r + j]],   o(i) = out_off + i,
@@ -432,11 +490,9 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
       const bool ready = !copies || wait_chunk(cons);  // each warp waits for the chunk itself
       const R* rows = reinterpret_cast<const R*>(sm.slots + size_t(slot) * sm.slot_bytes);
       const int cnt = min(rpc, it.count - ch * rpc);
-      for (int rr = ready ? warp : cnt; rr < cnt; rr += kWarps) {
-        const int ii = ch * rpc + rr;  // row within the item
+      // writes row ii of the item for this tile's RHS (lane t holds RHS t)
+      auto store_row = [&](int ii, const R (&acc)[RT][W]) {
         const int i = it.start + ii;
-        R acc[RT][W];
-        row_dot<R, C, RT>(rows + (long long)rr * ldt * W, xs, ldx_max, nvec, lane, acc);
         if (lane < nk) {
           const int t = lane;
           R val[W];
@@ -462,6 +518,29 @@ __device__ bool row_item(const RowArgs<R>& a, const MhtItem& it, const MhtBlockD
           }
 #pragma unroll
           for (int c = 0; c < W; ++c) out[(dst * a.os_e + (long long)(k0 + t) * a.os_k) * W + c] = val[c];
+        }
+      };
+      if constexpr (!C && RT >= 4) {
+        // pairs of rows (rr, rr + kWarps) share their staged-input loads
+        for (int rr = ready ? warp : cnt; rr < cnt; rr += 2 * kWarps) {
+          const int rr2 = rr + kWarps;
+          if (rr2 < cnt) {
+            R acca[RT][W], accb[RT][W];
+            row_dot2<R, RT>(rows + (long long)rr * ldt * W, rows + (long long)rr2 * ldt * W, xs, ldx_max, nvec, lane,
+                            acca, accb);
+            store_row(ch * rpc + rr, acca);
+            store_row(ch * rpc + rr2, accb);
+          } else {
+            R acc[RT][W];
+            row_dot<R, C, RT>(rows + (long long)rr * ldt * W, xs, ldx_max, nvec, lane, acc);
+            store_row(ch * rpc + rr, acc);
+          }
+        }
+      } else {
+        for (int rr = ready ? warp : cnt; rr < cnt; rr += kWarps) {
+          R acc[RT][W];
+          row_dot<R, C, RT>(rows + (long long)rr * ldt * W, xs, ldx_max, nvec, lane, acc);
+          store_row(ch * rpc + rr, acc);
         }
       }
       // one barrier per chunk: the slot (and after the tile's last chunk, xs / ident) is free
