@@ -88,7 +88,6 @@ struct StageDir {
   size_t desc_off = 0, items_off = 0;  // byte offsets in the image
   int64_t nitems = 0;
   int64_t max_ld = 0;                  // widest padded row (elements)
-  size_t max_tile_bytes = 0;           // largest work-item matrix tile
   int64_t max_item_rows = 0;           // most rows in one work item
   size_t data_bytes = 0;               // padded device bytes of this direction's matrices
   size_t tc_items_off = 0;             // 128-row tiles for the tensor-core stages

@@ -172,7 +172,6 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
         for (int r0 = 0; r0 < d.rows; r0 += rpi) {
           const int cnt = std::min(rpi, d.rows - r0);
           items[dir][s].push_back({int(b), r0, cnt, sib});
-          D.max_tile_bytes = std::max(D.max_tile_bytes, size_t(cnt) * rowbytes);
           D.max_item_rows = std::max<int64_t>(D.max_item_rows, cnt);
         }
       }
