@@ -80,7 +80,10 @@ typedef enum {
   MHT_ID_AUTO = 0,      /* BLOCKED for large problems (n m >= 2^28), else CLASSICAL          */
   MHT_ID_CLASSICAL = 1, /* Householder QR with column pivoting, one column at a time        */
   MHT_ID_BLOCKED = 2    /* QR with randomized block pivoting (Gaussian sketch of b + 8 rows
-                           picks 64 pivots at a time; compact-WY panel updates); large blocks */
+                           picks 64 pivots at a time; compact-WY panel updates) for blocks with
+                           min(M, K) >= 128, and a Gram-matrix pivoted-Cholesky certificate
+                           that skips the QR of very tall full-rank blocks (M >= 16 K);
+                           real and complex Phi                                              */
 } mht_id_method;
 
 typedef enum {
@@ -129,7 +132,7 @@ typedef struct {
   double oversample;   /* row-sampled IDs use min(|tau|, ceil(oversample * K) + 16) rows, a
                           heuristic that costs accuracy at tight eps; <= 0 disables
                           sampling (exact IDs on all rows, the recommended setting)     */
-  mht_id_method id_method; /* pivoting strategy of the real IDs (complex IDs: classical) */
+  mht_id_method id_method; /* pivoting strategy of the IDs                                */
 } mht_options;
 
 /* Factors as plain arrays: the content of a factorization, in the notation of Sec. 2.

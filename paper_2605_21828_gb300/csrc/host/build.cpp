@@ -115,7 +115,7 @@ Block factor_block(const Evaluator& ev, bool cplx, const std::vector<int64_t>& r
   if (cplx) {
     std::vector<std::complex<double>> A(size_t(M * K));
     ev.eval(rows->data(), M, cols.data(), K, reinterpret_cast<double*>(A.data()));
-    B.r = interpolative_decomposition_complex(A.data(), M, K, eps, B.perm, B.T);
+    B.r = interpolative_decomposition_complex(A.data(), M, K, eps, B.perm, B.T, seed ^ 0x5bd1e995ull, blocked);
   } else {
     std::vector<double> A(size_t(M * K));
     ev.eval(rows->data(), M, cols.data(), K, A.data());

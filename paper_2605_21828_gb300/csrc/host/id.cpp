@@ -145,6 +145,8 @@ int qrcp_id(S* A, int64_t M, int64_t K, double eps, std::vector<int32_t>& perm,
 // point where every remaining column norm is below that threshold.
 void gemm(bool transA, int m, int n, int k, double alpha, const double* A, int lda, const double* B, int ldb,
           double beta, double* C, int ldc);
+void zgemm(bool conjTransA, int m, int n, int k, std::complex<double> alpha, const std::complex<double>* A, int lda,
+           const std::complex<double>* B, int ldb, std::complex<double> beta, std::complex<double>* C, int ldc);
 
 namespace {
 
@@ -382,9 +384,231 @@ int interpolative_decomposition_real(double* A, int64_t M, int64_t K, double eps
   return qrcp_id<double>(A, M, K, eps, perm, T);
 }
 
+// ---------------------------------------------------------------------------------------
+// Complex counterparts of the blocked ID and of the full-rank certificate, same algorithms.
+// The reflectors are Hermitian, H = I - beta v v^H with beta = 2 / |v|^2 real and
+// H x = R_kk e_1 (R_kk = -phase(x_0) |x|), as in the classical complex QRCP above; their
+// product H_0 ... H_{b-1} = I - V T V^H has T upper triangular with T_qq = beta_q and
+// T(0:q, q) = -beta_q T(0:q, 0:q) V(:, 0:q)^H v_q, so Q^H A2 = A2 - V T^H (V^H A2).
+namespace {
+
+using cd = std::complex<double>;
+
+// Reflector of x (length n, n >= 1) in place: x becomes v (v_0 = x_0 - R_kk); returns beta.
+double zhouse(cd* x, int64_t n, cd* rkk) {
+  const double sig = sumsq(x, n);
+  const double alpha = std::sqrt(sig);
+  const double ax0 = std::abs(x[0]);
+  const cd phase = ax0 > 0 ? x[0] / ax0 : cd(1.0);
+  *rkk = -phase * alpha;
+  x[0] -= *rkk;
+  const double vn2 = 2.0 * alpha * (alpha + ax0);  // |x_0 + phase alpha|^2 + sig - |x_0|^2
+  return vn2 > 0 ? 2.0 / vn2 : 0.0;
+}
+
+void zsketch_pivots(std::vector<cd>& Y, int s, int k, int steps, std::vector<int>& swaps) {
+  std::vector<double> nr(k);
+  for (int j = 0; j < k; ++j) nr[j] = sumsq(&Y[size_t(j) * s], s);
+  swaps.assign(steps, 0);
+  for (int q = 0; q < steps; ++q) {
+    int p = q;
+    for (int j = q + 1; j < k; ++j)
+      if (nr[j] > nr[p]) p = j;
+    swaps[q] = p;
+    if (p != q) {
+      std::swap_ranges(&Y[size_t(q) * s], &Y[size_t(q + 1) * s], &Y[size_t(p) * s]);
+      std::swap(nr[q], nr[p]);
+    }
+    if (q >= s) continue;
+    cd* col = &Y[size_t(q) * s];
+    cd rkk;
+    const double beta = zhouse(col + q, s - q, &rkk);
+    if (beta != 0.0)
+      for (int j = q + 1; j < k; ++j) reflect(col + q, &Y[size_t(j) * s + q], s - q, beta);
+    col[q] = rkk;
+    for (int j = q + 1; j < k; ++j) nr[j] = std::max(0.0, nr[j] - std::norm(Y[size_t(j) * s + q]));
+  }
+}
+
+// X(:, c) = R^{-1} B(:, c) for the h x h upper-triangular R (ld ldr), column by column.
+void ztrsm_upper(const cd* R, int64_t ldr, int64_t h, cd* X, int64_t ldx, int64_t ncols) {
+  for (int64_t c = 0; c < ncols; ++c) {
+    cd* xc = X + c * ldx;
+    for (int64_t a = h - 1; a >= 0; --a) {
+      cd acc = xc[a];
+      for (int64_t q = a + 1; q < h; ++q) acc -= R[q * ldr + a] * xc[q];
+      xc[a] = acc / R[a * ldr + a];
+    }
+  }
+}
+
+int zqrcp_id_blocked(cd* A, int64_t M, int64_t K, double eps, uint64_t seed, std::vector<int32_t>& perm,
+                     std::vector<double>& Tout) {
+  constexpr int b = 64, p = 8, s = b + p;
+  perm.resize(K);
+  std::iota(perm.begin(), perm.end(), 0);
+  Tout.clear();
+  double maxn = 0;
+  for (int64_t j = 0; j < K; ++j) {
+    const double v = sumsq(A + j * M, M);
+    if (!std::isfinite(v)) fail(MHT_ERR_NUMERIC, "non-finite entry in a block of Phi");
+    maxn = std::max(maxn, v);
+  }
+  if (maxn == 0.0) return 0;
+  const double thr = eps * std::sqrt(maxn);
+  // complex Gaussian sketch Y = G A (s x K)
+  std::vector<cd> G(size_t(s) * M), Y(size_t(s) * K);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> N01;
+  for (auto& g : G) g = cd(N01(rng), N01(rng));
+  zgemm(false, s, int(K), int(M), 1.0, G.data(), s, A, int(M), 0.0, Y.data(), s);
+  const int64_t kmax = std::min(M, K);
+  int64_t r = kmax;
+  std::vector<cd> V, Tm, W, Ys, X;
+  std::vector<double> beta(b);
+  std::vector<int> swaps;
+  for (int64_t j = 0; j < kmax; j += b) {
+    const int bb = int(std::min<int64_t>(b, kmax - j));
+    const int64_t M2 = M - j, K2 = K - j - bb;
+    // a. pivots from the sketch of the remaining columns, replayed on A, Y and perm
+    Ys.assign(Y.begin() + size_t(j) * s, Y.end());
+    zsketch_pivots(Ys, s, int(K - j), bb, swaps);
+    for (int q = 0; q < bb; ++q) {
+      const int64_t a = j + q, c = j + swaps[q];
+      if (a == c) continue;
+      std::swap_ranges(A + a * M, A + (a + 1) * M, A + c * M);
+      std::swap_ranges(&Y[size_t(a) * s], &Y[size_t(a + 1) * s], &Y[size_t(c) * s]);
+      std::swap(perm[a], perm[c]);
+    }
+    // b. Householder QR of the panel; V keeps the reflectors (zero above their diagonal)
+    V.assign(size_t(M2) * bb, cd(0.0));
+    int64_t rank_here = -1;
+    for (int q = 0; q < bb; ++q) {
+      cd* col = A + (j + q) * M + j;
+      cd rkk;
+      beta[q] = zhouse(col + q, M2 - q, &rkk);
+      if (rank_here < 0 && !(std::abs(rkk) > thr)) rank_here = j + q;
+      cd* v = &V[size_t(q) * M2];
+      for (int64_t i = q; i < M2; ++i) v[i] = col[i];
+      if (beta[q] != 0.0)
+        for (int c = q + 1; c < bb; ++c) reflect(v + q, A + (j + c) * M + j + q, M2 - q, beta[q]);
+      col[q] = rkk;
+      for (int64_t i = q + 1; i < M2; ++i) col[i] = cd(0.0);
+    }
+    // c. T of the compact WY form
+    Tm.assign(size_t(bb) * bb, cd(0.0));
+    std::vector<cd> w(bb);
+    for (int q = 0; q < bb; ++q) {
+      Tm[size_t(q) * bb + q] = beta[q];
+      if (q == 0 || beta[q] == 0.0) continue;
+      const cd* vq = &V[size_t(q) * M2];
+      for (int c = 0; c < q; ++c) {  // w = -beta_q V(:, 0:q)^H v_q (v_q is zero above row q)
+        const cd* vc = &V[size_t(c) * M2];
+        cd acc = 0;
+        for (int64_t i = q; i < M2; ++i) acc += std::conj(vc[i]) * vq[i];
+        w[c] = -beta[q] * acc;
+      }
+      for (int a = 0; a < q; ++a) {
+        cd acc = 0;
+        for (int c = a; c < q; ++c) acc += Tm[size_t(c) * bb + a] * w[c];
+        Tm[size_t(q) * bb + a] = acc;
+      }
+    }
+    // d. trailing update A2 <- A2 - V T^H (V^H A2)
+    cd* A2 = A + (j + bb) * M + j;
+    if (K2 > 0) {
+      W.assign(size_t(bb) * K2, cd(0.0));
+      zgemm(true, bb, int(K2), int(M2), 1.0, V.data(), int(M2), A2, int(M), 0.0, W.data(), bb);
+      for (int64_t c = 0; c < K2; ++c) {  // W <- T^H W, bottom row first (T^H is lower triangular)
+        cd* wc = &W[size_t(c) * bb];
+        for (int a = bb - 1; a >= 0; --a) {
+          cd acc = 0;
+          for (int q = 0; q <= a; ++q) acc += std::conj(Tm[size_t(a) * bb + q]) * wc[q];
+          wc[a] = acc;
+        }
+      }
+      zgemm(false, int(M2), int(K2), bb, -1.0, V.data(), int(M2), W.data(), bb, 1.0, A2, int(M));
+    }
+    if (rank_here >= 0) { r = rank_here; break; }
+    // e. stop when every remaining column is below the threshold
+    double rem = 0;
+    for (int64_t c = 0; c < K2; ++c) rem = std::max(rem, sumsq(A2 + c * M + bb, M2 - bb));
+    if (K2 == 0 || std::sqrt(rem) <= thr || j + bb >= kmax) { r = std::min<int64_t>(j + bb, kmax); break; }
+    // f. sketch downdate Y2 <- Y2 - Y1 R11^{-1} R12
+    X.assign(size_t(bb) * K2, cd(0.0));
+    for (int64_t c = 0; c < K2; ++c)
+      for (int a = 0; a < bb; ++a) X[size_t(c) * bb + a] = A2[c * M + a];
+    ztrsm_upper(A + j * M + j, M, bb, X.data(), bb, K2);
+    zgemm(false, s, int(K2), bb, -1.0, &Y[size_t(j) * s], s, X.data(), bb, 1.0, &Y[size_t(j + bb) * s], s);
+  }
+  // T~ = R11^{-1} R12 by blocked back substitution, written row-major r x (K - r)
+  const int64_t nc = K - r;
+  Tout.assign(size_t(r * nc) * 2, 0.0);
+  if (r == 0 || nc == 0) return int(r);
+  std::vector<cd> Tc(size_t(r) * nc);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int64_t i = 0; i < r; ++i) Tc[size_t(c) * r + i] = A[(r + c) * M + i];
+  constexpr int bs = 64;
+  for (int64_t i1 = r; i1 > 0; i1 -= bs) {
+    const int64_t i0 = std::max<int64_t>(0, i1 - bs), h = i1 - i0;
+    if (i1 < r)
+      zgemm(false, int(h), int(nc), int(r - i1), -1.0, A + i1 * M + i0, int(M), &Tc[i1], int(r), 1.0, &Tc[i0],
+            int(r));
+    ztrsm_upper(A + i0 * M + i0, M, h, &Tc[i0], r, nc);
+  }
+  cd* T = reinterpret_cast<cd*>(Tout.data());
+  for (int64_t i = 0; i < r; ++i)
+    for (int64_t c = 0; c < nc; ++c) T[size_t(i) * nc + c] = Tc[size_t(c) * r + i];
+  for (double v : Tout)
+    if (!std::isfinite(v)) fail(MHT_ERR_NUMERIC, "non-finite interpolation coefficient");
+  return int(r);
+}
+
+// Complex full-rank certificate: Hermitian Gram matrix A^H A and diagonally pivoted Cholesky,
+// same decision rule as the real one.
+bool certify_full_rank_complex(const cd* A, int64_t M, int64_t K, double eps) {
+  std::vector<cd> G(size_t(K) * K);
+  zgemm(true, int(K), int(K), int(M), 1.0, A, int(M), A, int(M), 0.0, G.data(), int(K));
+  double dmax = 0;
+  for (int64_t j = 0; j < K; ++j) dmax = std::max(dmax, G[j * K + j].real());
+  if (!(dmax > 0) || !std::isfinite(dmax)) return false;
+  const double floor = 100.0 * eps * eps * dmax;
+  std::vector<int64_t> piv(K);
+  std::iota(piv.begin(), piv.end(), int64_t(0));
+  std::vector<double> d(K);
+  for (int64_t j = 0; j < K; ++j) d[j] = G[j * K + j].real();
+  std::vector<cd> Lc(size_t(K) * K, cd(0.0));  // Lc[q K + i] = L(i, q)
+  for (int64_t k = 0; k < K; ++k) {
+    int64_t p = k;
+    for (int64_t j = k + 1; j < K; ++j)
+      if (d[piv[j]] > d[piv[p]]) p = j;
+    std::swap(piv[k], piv[p]);
+    const double pk = d[piv[k]];
+    if (!(pk > floor)) return false;
+    const double lkk = std::sqrt(pk);
+    for (int64_t j = k + 1; j < K; ++j) {
+      cd v = G[piv[k] * K + piv[j]];  // G(piv_j, piv_k)
+      for (int64_t q = 0; q < k; ++q) v -= Lc[q * K + piv[j]] * std::conj(Lc[q * K + piv[k]]);
+      v /= lkk;
+      Lc[k * K + piv[j]] = v;
+      d[piv[j]] -= std::norm(v);
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
 int interpolative_decomposition_complex(std::complex<double>* A, int64_t M, int64_t K,
                                         double eps, std::vector<int32_t>& perm,
-                                        std::vector<double>& T) {
+                                        std::vector<double>& T, uint64_t seed, bool blocked) {
+  if (blocked && K >= 32 && M >= 16 * K && certify_full_rank_complex(A, M, K, eps)) {
+    perm.resize(K);
+    std::iota(perm.begin(), perm.end(), 0);
+    T.clear();
+    return int(K);
+  }
+  if (blocked && std::min(M, K) >= 128) return zqrcp_id_blocked(A, M, K, eps, seed, perm, T);
   return qrcp_id<std::complex<double>>(A, M, K, eps, perm, T);
 }
 

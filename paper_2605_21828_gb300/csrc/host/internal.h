@@ -68,13 +68,14 @@ void space_tree(const mht_problem& p, mht_tree_kind kind, int L, uint64_t seed,
 // Column ID of the column-major M x K matrix A (overwritten) by Householder QR with column
 // pivoting; rank = #{k : |R_kk| > eps |R_11|}.  Writes perm (skeleton first) and
 // T~ = R11^{-1} R12 (row-major r x (K-r)).  Returns r.
-// blocked = true selects the randomized block-pivoted variant (HQRRP) for large blocks.
+// blocked = true selects the randomized block-pivoted variant (HQRRP) for large blocks and a
+// Gram-matrix full-rank certificate for very tall ones (real and complex).
 int interpolative_decomposition_real(double* A, int64_t M, int64_t K, double eps,
                                      std::vector<int32_t>& perm, std::vector<double>& T, uint64_t seed = 0,
                                      bool blocked = false);
 int interpolative_decomposition_complex(std::complex<double>* A, int64_t M, int64_t K,
                                         double eps, std::vector<int32_t>& perm,
-                                        std::vector<double>& T);
+                                        std::vector<double>& T, uint64_t seed = 0, bool blocked = false);
 
 // --- build ---------------------------------------------------------------------------------
 void build_factorization(const mht_problem& p, const mht_options& o, Factorization& F);

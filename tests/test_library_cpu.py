@@ -238,6 +238,27 @@ def test_blocked_randomized_pivoting_id_matches_dense(mht_lib):
     assert errs["blocked"] < 10 * eps and errs["classical"] < 10 * eps
 
 
+def test_blocked_complex_id_matches_dense(mht_lib):
+    # complex Phi (flat torus): the block-pivoted complex ID and the Gram full-rank certificate
+    # (leaf blocks with M >= 16 K) keep the accuracy and the ranks of the classical QRCP
+    n, eps = 2304, 1e-6
+    K, X = W.torus_modes(n), W.torus_points(n)
+    Phi = H.torus_phi(X, K)
+    ranks = {}
+    for meth in ("blocked", "classical"):
+        p = _plan_cls().build(n=n, m=n, eigenvalues=W.torus_eigenvalues(K), evaluator="torus", points=X,
+                              torus_modes=K, eps=eps, leaf_size=32, id_method=meth)
+        F = arrays_to_oracle(p.export())
+        ranks[meth] = int(np.sum(p.export()["ranks"]))
+        c = W.gaussian(n, 3, complex_=True)
+        ref = Phi @ c
+        assert np.linalg.norm(B.synthesize(F, c) - ref) / np.linalg.norm(ref) < 10 * eps, meth
+        g = W.gaussian(n, 4, complex_=True)
+        refa = Phi.conj().T @ g
+        assert np.linalg.norm(B.analyze(F, g) - refa) / np.linalg.norm(refa) < 10 * eps, meth
+    assert abs(ranks["blocked"] - ranks["classical"]) <= 0.01 * ranks["classical"]
+
+
 def test_clone_and_set_mode(mht_lib):
     from paper_2605_21828_gb300 import MhtError
     n = 256
