@@ -29,12 +29,12 @@ METRIC = "transforms/s (synthesis + weighted adjoint)"
 # DRAM bytes (read + write) per algorithmic byte of the per-stage kernel, from ncu's
 # dram__bytes_read.sum + dram__bytes_write.sum over every stage launch of one timed step on the
 # 16384-point sphere (the launch shapes the autotuner chose there).  Traffic grows in proportion
-# to the bytes a launch streams (1.002 on the largest 16384-point stages), so a full-size
+# to the bytes a launch streams (1.001 on the largest 16384-point stages), so a full-size
 # launch's traffic is this ratio times its algorithmic bytes.  None: not captured for the
 # current kernel.
 NCU_DRAM_PER_ALG_BYTE = {
-    "k_rowdot synthesis (transfer levels 0..L)": 1.0006,
-    "k_rowdot adjoint (transfer levels L..0)": 1.0033,
+    "k_rowdot synthesis (transfer levels 0..L)": 0.9998,
+    "k_rowdot adjoint (transfer levels L..0)": 1.0034,
 }
 WORKLOADS = {
     # name: (n, lmax, leaf, eps)
