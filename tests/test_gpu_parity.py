@@ -229,6 +229,48 @@ def test_library_build_plus_gpu_torus_fp64_config(torch_cuda):
     assert _rel(a, Phi.conj().T @ g)[0] < 10 * eps
 
 
+_FEM = {}
+
+
+def _fem_problem():
+    # deformed icosphere (4 subdivisions, 2562 vertices), 1024 lowest P1 FEM eigenpairs,
+    # M-orthonormal; the shape of the deformed-sphere workload at a size the oracle's dense
+    # generalized eigensolver handles in seconds
+    if not _FEM:
+        from oracle import fem
+        V, F_ = W.deformed_icosphere(4)
+        lam, Phi, Md, _ = fem.laplace_beltrami_basis(V, F_, 1024)
+        _FEM.update(V=V, lam=lam, Phi=Phi, Md=Md)
+    return _FEM
+
+
+@pytest.mark.parametrize("mode", ["fp32", "3xtf32"])
+@pytest.mark.parametrize("nrhs", [1, 64])
+def test_fem_deformed_sphere_matches_oracle_and_inverts(torch_cuda, mode, nrhs):
+    from paper_2605_21828_gb300 import Plan
+    from tests._bridge import arrays_to_oracle
+    torch = torch_cuda
+    P = _fem_problem()
+    Phi, Md = P["Phi"], P["Md"]
+    n, m = Phi.shape
+    eps = 1e-6
+    plan = Plan.build(n=n, m=m, eigenvalues=P["lam"], evaluator="dense", dense=Phi, points=P["V"], eps=eps,
+                      leaf_size=64, mode=mode, weights=Md).bind(max_nrhs=nrhs)
+    F = arrays_to_oracle(plan.export())
+    C_ = W.gaussian_columns(m, nrhs, 51)
+    f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
+    assert plan.check() == 0
+    _check(f, B.synthesize(F, C_), mode)  # kernel error: the oracle's FP64 apply of the same plan
+    assert _rel(f, Phi @ C_)[0] < 10 * eps + TOL[mode]  # compression error: the dense transform
+    G = W.gaussian_columns(n, nrhs, 52)
+    a = plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy()
+    assert plan.check() == 0
+    _check(a, B.analyze(F, G, Md), mode)
+    # Phi^T M Phi = I: weighted analysis undoes synthesis up to the two compression errors
+    c2 = plan.analyze_raw(_to_dev(torch, f, plan), weighted=True).cpu().numpy()
+    assert _rel(c2, C_)[0] < 20 * eps
+
+
 def test_autograd_matches_adjoint_and_finite_differences(torch_cuda):
     from paper_2605_21828_gb300 import Plan, analyze, synthesize
     torch = torch_cuda
