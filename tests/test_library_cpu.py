@@ -259,6 +259,33 @@ def test_blocked_complex_id_matches_dense(mht_lib):
     assert abs(ranks["blocked"] - ranks["classical"]) <= 0.01 * ranks["classical"]
 
 
+def test_ranks_match_the_oracle_build_on_the_same_trees(mht_lib):
+    # the library's build against the oracle's independent build (scipy pivoted QR) of the
+    # same blocks: same space tree (handed in), same frequency order, same rank rule
+    X = W.fibonacci_points(1024)
+    Phi = H.sphere_phi(X, 31)
+    lam = W.sphere_eigenvalues(1024)
+    F = B.build(B.dense_evaluator(Phi), 1024, 1024, lam, X, 1e-6, 64)
+    p = _plan_cls().build(n=1024, m=1024, eigenvalues=lam, evaluator="sphere", points=X, eps=1e-6, leaf_size=64,
+                          space=(F.space_perm, F.space_off), id_method="classical")
+    e = p.export()
+    assert np.array_equal(e["mode_perm"], F.mode_perm)
+    lib = np.asarray(e["ranks"]).reshape(F.L + 1, -1)
+    assert np.array_equal(lib, np.array([np.asarray(r) for r in F.ranks]))  # block by block
+    # complex exponentials all have the same column norm, so the first pivot of every block is
+    # a tie that rounding decides; ranks may then differ by a column or two per block
+    Xt, K = W.torus_points(1024), W.torus_modes(1024)
+    lt = W.torus_eigenvalues(K)
+    Ft = B.build(B.dense_evaluator(H.torus_phi(Xt, K)), 1024, 1024, lt, Xt, 1e-8, 64, "rect", complex_=True)
+    for meth in ("classical", "blocked"):
+        pt = _plan_cls().build(n=1024, m=1024, eigenvalues=lt, evaluator="torus", points=Xt, torus_modes=K, eps=1e-8,
+                               leaf_size=64, space=(Ft.space_perm, Ft.space_off), id_method=meth)
+        lib = np.asarray(pt.export()["ranks"]).reshape(Ft.L + 1, -1)
+        ora = np.array([np.asarray(r) for r in Ft.ranks])
+        assert np.abs(lib - ora).max() <= 2, meth
+        assert np.all(np.abs(lib.sum(axis=1) - ora.sum(axis=1)) <= 0.005 * ora.sum(axis=1)), meth
+
+
 def test_clone_and_set_mode(mht_lib):
     from paper_2605_21828_gb300 import MhtError
     n = 256
