@@ -118,22 +118,39 @@ struct SphereEval : Evaluator {
       sr[i] = s[rows[i]];
     }
     const double root2 = std::sqrt(2.0);
+    // The orders are visited in increasing |mm| (std::map order), so Pbar_am^am continues from
+    // the previous order's product, and cos / sin(am lon) advance by one rotation through lon
+    // when am is the next order; they are recomputed directly every 16 orders and after a gap,
+    // which bounds the rotations' rounding to a few ulps.
+    std::vector<double> c1(nr), s1(nr);
+    for (int64_t i = 0; i < nr; ++i) {
+      pmm[i] = 1.0 / std::sqrt(4.0 * M_PI);
+      c1[i] = std::cos(lon[rows[i]]);
+      s1[i] = std::sin(lon[rows[i]]);
+    }
+    int64_t am_prev = -2;
     for (auto& kv : groups) {
       const int64_t am = kv.first;
       auto& list = kv.second;
       int64_t lmax = 0;
       for (auto& e : list) lmax = std::max(lmax, e[0]);
-      // Pbar_am^am
-      double c = 1.0 / std::sqrt(4.0 * M_PI);
-      for (int64_t i = 0; i < nr; ++i) pmm[i] = c;
-      for (int64_t k = 1; k <= am; ++k) {
+      for (int64_t k = std::max<int64_t>(am_prev, 0) + 1; k <= am; ++k) {
         const double f = std::sqrt((2.0 * k + 1.0) / (2.0 * k));
         for (int64_t i = 0; i < nr; ++i) pmm[i] *= f * sr[i];
       }
-      for (int64_t i = 0; i < nr; ++i) {
-        cosm[i] = std::cos(double(am) * lon[rows[i]]);
-        sinm[i] = std::sin(double(am) * lon[rows[i]]);
+      if (am == am_prev + 1 && am % 16 != 0) {
+        for (int64_t i = 0; i < nr; ++i) {
+          const double cn = cosm[i] * c1[i] - sinm[i] * s1[i];
+          sinm[i] = sinm[i] * c1[i] + cosm[i] * s1[i];
+          cosm[i] = cn;
+        }
+      } else {
+        for (int64_t i = 0; i < nr; ++i) {
+          cosm[i] = std::cos(double(am) * lon[rows[i]]);
+          sinm[i] = std::sin(double(am) * lon[rows[i]]);
+        }
       }
+      am_prev = am;
       // emit columns as the recurrence passes their degree
       std::sort(list.begin(), list.end());
       size_t next = 0;
