@@ -71,24 +71,25 @@ def workload_desc(name):
     return {"workload": f"unit sphere: n={n} jittered-Fibonacci points, m={(lmax + 1) ** 2} real spherical "
                         f"harmonics (degree <= {lmax}), eps={eps:g}, leaf {leaf}, FP32 factors, weights 4pi/n",
             "n": n, "m": (lmax + 1) ** 2, "eps": eps, "leaf_size": leaf,
-            "l2": "packed factors >> 129 MB L2 (streamed from HBM every step; no flush needed)"}
+            "l2": ("packed factors >> 129 MB L2 (streamed from HBM every step; no flush needed)" if n >= 16384 else
+                   "packed factors may fit in the 129 MB L2 (L2-resident small case; not a bench line)")}
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
 def oracle_sample_step(X, c, w, rows, lmax):
     """Oracle direct summation restricted to `rows`: f(rows) = Phi(rows,:) c and the
-    contribution Phi(rows,:)^T (w f)(rows) to the adjoint.  Returns seconds."""
+    contribution Phi(rows,:)^T (w f)(rows) to the adjoint.  Returns (wall, process CPU) seconds."""
     import numpy as np
 
     from oracle import harmonics as H
-    t0 = time.perf_counter()
+    t0, p0 = time.perf_counter(), time.process_time()
     Phi = H.sphere_phi(X[rows], lmax)
     f = Phi @ c
     _ = Phi.T @ (w[rows] * f)
-    dt = time.perf_counter() - t0
+    dt, cpu = time.perf_counter() - t0, time.process_time() - p0
     del Phi
     np.asarray(f)
-    return dt
+    return dt, cpu
 
 
 def cpu_baseline(name, budget_s=15.0, steps=None):
@@ -102,17 +103,22 @@ def cpu_baseline(name, budget_s=15.0, steps=None):
     w = np.full(n, 4 * np.pi / n)
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(n, 256, replace=False))
-    t = oracle_sample_step(X, c, w, rows, lmax)
+    t, _ = oracle_sample_step(X, c, w, rows, lmax)
     per_row = t / len(rows)
     s = int(min(n, max(256, budget_s / max(per_row, 1e-9) / (steps or 1))))
     rows = np.sort(rng.choice(n, s, replace=False))
-    times = [oracle_sample_step(X, c, w, rows, lmax) for _ in range(steps or 1)]
+    runs = [oracle_sample_step(X, c, w, rows, lmax) for _ in range(steps or 1)]
+    times = [r[0] for r in runs]
     t_full = statistics.median(times) * n / s
-    cores = len(os.sched_getaffinity(0))
-    return 1.0 / t_full, {"kind": "oracle", "cores": cores,
+    avail = len(os.sched_getaffinity(0))
+    # threads actually used: process CPU time over wall time (the numpy recurrence runs on
+    # one thread, the BLAS products on several)
+    used = sum(r[1] for r in runs) / max(sum(times), 1e-9)
+    return 1.0 / t_full, {"kind": "oracle", "cores": max(1, round(used)), "cpu_time_per_wall_time": round(used, 2),
+                          "cores_available": avail,
                           "sample": f"{s} of {n} rows per step (Phi rows by the normalized Legendre recurrence, "
-                                    f"f = Phi c and Phi^T W f restricted to them), scaled by n/{s}; numpy/BLAS "
-                                    f"threads on {cores} cores"}, times
+                                    f"f = Phi c and Phi^T W f restricted to them), scaled by n/{s}; numpy "
+                                    f"(one thread) and BLAS (up to {avail} threads)"}, times
 
 
 def run_reference(args):
