@@ -586,8 +586,6 @@ mht_status mht_destroy(mht_plan* plan) {
   return MHT_OK;
 }
 
-}  // extern "C"
-
 // ---- batched apply ---------------------------------------------------------------------
 
 mht_status mht_batch_create(mht_plan* const* plans, int32_t count, const int64_t* nrhs, mht_batch** out) {
@@ -682,7 +680,7 @@ mht_status mht_batch_set_io(mht_batch* batch, void* const* c_dev, const int64_t*
 }
 
 namespace {
-mht_status batch_run(mht_batch* batch, int dir, bool weighted, void* stream) {
+static mht_status batch_run(mht_batch* batch, int dir, bool weighted, void* stream) {
   if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
   if (!batch->bound || !batch->io_set) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound or has no vectors");
   std::string err;
@@ -807,3 +805,5 @@ mht_status mht_batch_destroy(mht_batch* batch) {
   delete batch;
   return MHT_OK;
 }
+
+}  // extern "C"
