@@ -196,6 +196,16 @@ typedef struct {
 mht_status mht_build_plan(const mht_problem* problem, const mht_options* options,
                           mht_plan** out);
 
+/* Entries Phi(rows, cols) of the problem's evaluator -- the values mht_build_plan factors
+ * (Sec. 1, Eq. MHT-sum: Phi_jk = phi_k(x_j)) -- in FP64, column-major out[nrows * ncols],
+ * interleaved (re, im) when problem->field is MHT_COMPLEX.  rows are original point indices
+ * in [0, n), cols original mode indices in [0, m); out is caller-owned host memory.  Only the
+ * evaluator fields of the problem are read (eigenvalues and weights are not needed).
+ * Errors: INVALID_ARG (NULL pointers, negative counts, indices out of range, missing
+ * evaluator data), CALLBACK. */
+mht_status mht_problem_eval(const mht_problem* problem, const int64_t* rows, int64_t nrows,
+                            const int64_t* cols, int64_t ncols, double* out);
+
 /* Creates a plan from explicit factors (layout above); the arrays are copied and may be
  * freed after the call.  options->mode selects the apply precision; other option fields
  * are ignored.  Errors: INVALID_ARG, FORMAT (inconsistent ranks, permutations, offsets). */

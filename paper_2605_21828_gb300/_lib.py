@@ -64,6 +64,8 @@ class LevelInfo(C.Structure):
 # name -> (restype, argtypes); every entry point declared in include/mht.h
 SIGNATURES = {
     "mht_build_plan": (C.c_int, [C.POINTER(Problem), C.POINTER(Options), C.POINTER(C.c_void_p)]),
+    "mht_problem_eval": (C.c_int, [C.POINTER(Problem), C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64),
+                                   C.c_int64, C.POINTER(C.c_double)]),
     "mht_plan_import": (C.c_int, [C.POINTER(Factors), C.POINTER(Options), C.POINTER(C.c_void_p)]),
     "mht_plan_export": (C.c_int, [C.c_void_p, C.POINTER(Factors)]),
     "mht_plan_info": (C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),

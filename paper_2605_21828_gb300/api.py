@@ -37,6 +37,76 @@ def _options(eps=1e-6, leaf_size=128, levels=-1, mode="fp32", tree="auto", seed=
                      oversample, _IDS[id_method])
 
 
+def _problem(*, n, m, evaluator, points=None, torus_modes=None, dense=None, callback=None, complex_=None):
+    """An mht_problem with the evaluator fields set; returns (problem, arrays to keep alive, complex)."""
+    prob = L.Problem()
+    keep = []
+    if complex_ is None:
+        complex_ = evaluator == "torus" or (dense is not None and np.iscomplexobj(dense))
+    prob.n, prob.m = n, m
+    prob.field = L.COMPLEX if complex_ else L.REAL
+    if points is not None:
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        keep.append(pts)
+        prob.points = _dptr(pts, C.c_double)
+        prob.dim = pts.shape[1]
+    if evaluator == "callback":
+        prob.eval_kind = L.EVAL_CALLBACK
+
+        def _cb(ctx, rows, nr, cols, nc, out):
+            try:
+                r = np.ctypeslib.as_array(rows, (nr,)).copy()
+                cc = np.ctypeslib.as_array(cols, (nc,)).copy()
+                blk = np.asarray(callback(r, cc))
+                o = np.ctypeslib.as_array(out, (nr * nc * (2 if complex_ else 1),))
+                if complex_:  # column-major, interleaved (re, im)
+                    o[:] = np.ascontiguousarray(blk.astype(np.complex128).T).view(np.float64).reshape(-1)
+                else:
+                    o[:] = np.asarray(blk, dtype=np.float64).T.reshape(-1)
+                return 0
+            except Exception:  # noqa: BLE001 - reported to the library as a failure
+                return 1
+
+        fn = L.EVAL_FN(_cb)
+        keep.append(fn)
+        prob.eval = fn
+    else:
+        prob.eval_kind = _EVALS[evaluator]
+    if torus_modes is not None:
+        km = np.ascontiguousarray(torus_modes, dtype=np.int64)
+        keep.append(km)
+        prob.torus_modes = _dptr(km, C.c_int64)
+    if dense is not None:
+        if complex_:
+            D = np.asfortranarray(dense, dtype=np.complex128)
+            flat = D.reshape(-1, order="F").view(np.float64)
+        else:
+            D = np.asfortranarray(dense, dtype=np.float64)
+            flat = D.reshape(-1, order="F")
+        keep += [D, flat]
+        prob.dense = _dptr(flat, C.c_double)
+        prob.ld_dense = n
+    return prob, keep, complex_
+
+
+def phi_entries(rows, cols, *, n, m, evaluator="sphere", points=None, torus_modes=None, dense=None,
+                callback=None, complex_=None) -> np.ndarray:
+    """Phi(rows, cols) from the library's evaluator (``mht_problem_eval``): the FP64 values a
+    build factors, as a (len(rows), len(cols)) float64 or complex128 array."""
+    lib = L.load()
+    prob, keep, cplx = _problem(n=n, m=m, evaluator=evaluator, points=points, torus_modes=torus_modes,
+                                dense=dense, callback=callback, complex_=complex_)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    c = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.zeros(len(r) * len(c) * (2 if cplx else 1), dtype=np.float64)
+    L.check(lib.mht_problem_eval(C.byref(prob), _dptr(r, C.c_int64), len(r), _dptr(c, C.c_int64), len(c),
+                                 _dptr(out, C.c_double)))
+    del keep
+    if cplx:
+        return out.view(np.complex128).reshape(len(c), len(r)).T
+    return out.reshape(len(c), len(r)).T
+
+
 class Plan:
     """A built (or imported) butterfly factorization and, once bound, its device copy."""
 
@@ -60,55 +130,11 @@ class Plan:
         selects tree="given".
         """
         lib = L.load()
+        prob, keep, _ = _problem(n=n, m=m, evaluator=evaluator, points=points, torus_modes=torus_modes,
+                                 dense=dense, callback=callback, complex_=complex_)
         lam = np.ascontiguousarray(eigenvalues, dtype=np.float64)
-        keep = [lam]
-        if complex_ is None:
-            complex_ = evaluator == "torus" or (dense is not None and np.iscomplexobj(dense))
-        prob = L.Problem()
-        prob.n, prob.m = n, m
-        prob.field = L.COMPLEX if complex_ else L.REAL
+        keep.append(lam)
         prob.eigenvalues = _dptr(lam, C.c_double)
-        if points is not None:
-            pts = np.ascontiguousarray(points, dtype=np.float64)
-            keep.append(pts)
-            prob.points = _dptr(pts, C.c_double)
-            prob.dim = pts.shape[1]
-        if evaluator == "callback":
-            prob.eval_kind = L.EVAL_CALLBACK
-
-            def _cb(ctx, rows, nr, cols, nc, out):
-                try:
-                    r = np.ctypeslib.as_array(rows, (nr,)).copy()
-                    cc = np.ctypeslib.as_array(cols, (nc,)).copy()
-                    blk = np.asarray(callback(r, cc))
-                    o = np.ctypeslib.as_array(out, (nr * nc * (2 if complex_ else 1),))
-                    if complex_:  # column-major, interleaved (re, im)
-                        o[:] = np.ascontiguousarray(blk.astype(np.complex128).T).view(np.float64).reshape(-1)
-                    else:
-                        o[:] = np.asarray(blk, dtype=np.float64).T.reshape(-1)
-                    return 0
-                except Exception:  # noqa: BLE001 - reported to the library as a failure
-                    return 1
-
-            fn = L.EVAL_FN(_cb)
-            keep.append(fn)
-            prob.eval = fn
-        else:
-            prob.eval_kind = _EVALS[evaluator]
-        if torus_modes is not None:
-            km = np.ascontiguousarray(torus_modes, dtype=np.int64)
-            keep.append(km)
-            prob.torus_modes = _dptr(km, C.c_int64)
-        if dense is not None:
-            if complex_:
-                D = np.asfortranarray(dense, dtype=np.complex128)
-                flat = D.reshape(-1, order="F").view(np.float64)
-            else:
-                D = np.asfortranarray(dense, dtype=np.float64)
-                flat = D.reshape(-1, order="F")
-            keep += [D, flat]
-            prob.dense = _dptr(flat, C.c_double)
-            prob.ld_dense = n
         if weights is not None:
             w = np.ascontiguousarray(weights, dtype=np.float64)
             keep.append(w)

@@ -110,6 +110,22 @@ mht_status mht_build_plan(const mht_problem* problem, const mht_options* options
   });
 }
 
+mht_status mht_problem_eval(const mht_problem* problem, const int64_t* rows, int64_t nrows, const int64_t* cols,
+                            int64_t ncols, double* out) {
+  return guarded([&]() -> mht_status {
+    if (!problem || nrows < 0 || ncols < 0) mht::fail(MHT_ERR_INVALID_ARG, "bad argument");
+    if (nrows == 0 || ncols == 0) return MHT_OK;
+    if (!rows || !cols || !out) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    for (int64_t i = 0; i < nrows; ++i)
+      if (rows[i] < 0 || rows[i] >= problem->n) mht::fail(MHT_ERR_INVALID_ARG, "row index out of range");
+    for (int64_t j = 0; j < ncols; ++j)
+      if (cols[j] < 0 || cols[j] >= problem->m) mht::fail(MHT_ERR_INVALID_ARG, "column index out of range");
+    std::unique_ptr<mht::Evaluator> ev(mht::make_evaluator(*problem));
+    ev->eval(rows, nrows, cols, ncols, out);
+    return MHT_OK;
+  });
+}
+
 mht_status mht_plan_import(const mht_factors* factors, const mht_options* options, mht_plan** out) {
   return guarded([&]() -> mht_status {
     if (!factors || !options || !out) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");

@@ -103,6 +103,29 @@ def test_fiedler_tree_separates_clusters(mht_lib):
     assert left in (set(range(40)), set(range(40, 80)))
 
 
+def test_library_evaluator_matches_the_oracle_harmonics(mht_lib):
+    # the entries the build factors: real spherical harmonics up to degree 255 (every order, so
+    # the order-to-order recurrences of the library's evaluator are all exercised) and complex
+    # exponentials, against the oracle's independent closed forms (themselves pinned to scipy
+    # and the FFT)
+    from paper_2605_21828_gb300 import MhtError, phi_entries
+    X = W.fibonacci_points(300, seed=4)
+    P = H.sphere_phi(X, 255)
+    Q = phi_entries(np.arange(300), np.arange(65536), n=300, m=65536, evaluator="sphere", points=X)
+    assert np.abs(Q - P).max() < 1e-12
+    rng = np.random.default_rng(1)
+    rows, cols = rng.permutation(300)[:200], rng.choice(65536, 5000, replace=False)  # gaps, any order
+    Q2 = phi_entries(rows, cols, n=300, m=65536, evaluator="sphere", points=X)
+    assert np.abs(Q2 - P[np.ix_(rows, cols)]).max() < 1e-12
+    Xt, K = W.torus_points(500), W.torus_modes(4096)
+    Qt = phi_entries(np.arange(500), np.arange(4096), n=500, m=4096, evaluator="torus", points=Xt, torus_modes=K)
+    assert Qt.dtype == np.complex128 and np.abs(Qt - H.torus_phi(Xt, K)).max() < 1e-12
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        phi_entries([300], [0], n=300, m=65536, evaluator="sphere", points=X)
+    with pytest.raises(MhtError, match="INVALID_ARG"):
+        phi_entries([0], [65536], n=300, m=65536, evaluator="sphere", points=X)
+
+
 def test_import_export_roundtrip(mht_lib):
     n = 256
     X, Phi, lam = _sphere(n, 15)
