@@ -309,6 +309,24 @@ def test_ranks_match_the_oracle_build_on_the_same_trees(mht_lib):
         assert np.all(np.abs(lib.sum(axis=1) - ora.sum(axis=1)) <= 0.005 * ora.sum(axis=1)), meth
 
 
+def test_library_level_structure_matches_the_papers_figure(mht_lib):
+    # Fig. BF-levels (Sec. 2, tests/golden/bf_levels_L3.txt): at level l the library factors the
+    # block of the space node at depth l and the frequency node at height l; with a Gaussian
+    # Phi and unequal leaf sizes every block's ID rank is min(|tau|, |nu|)
+    from tests.test_oracle_butterfly import _expected_rank_for, _figure_blocks
+    G = _figure_blocks()
+    sx, sw, L = 32, 8, 3
+    n, m = 8 * sx, 8 * sw
+    Phi = np.random.default_rng(7).standard_normal((n, m))
+    p = _plan_cls().build(n=n, m=m, eigenvalues=np.arange(m, dtype=float), evaluator="dense", dense=Phi,
+                          eps=1e-12, leaf_size=sx, space=(np.arange(n), np.arange(0, n + 1, sx)))
+    ranks = np.asarray(p.export()["ranks"]).reshape(L + 1, 8)
+    for l in range(L + 1):
+        nb = 1 << (L - l)
+        for b in range(8):
+            assert ranks[l, b] == _expected_rank_for(G[l], L, l, b // nb, b % nb, sx, sw)
+
+
 def test_clone_and_set_mode(mht_lib):
     from paper_2605_21828_gb300 import MhtError
     n = 256

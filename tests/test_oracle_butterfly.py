@@ -160,3 +160,43 @@ def test_multiple_right_hand_sides_are_columnwise():
     Fm = B.synthesize(F, C)
     for j in range(3):
         assert np.allclose(Fm[:, j], B.synthesize(F, C[:, j]))
+
+
+def _figure_blocks():
+    """Blocks of Fig. BF-levels (Sec. 2), transcribed in tests/golden/bf_levels_L3.txt."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bf_levels_L3.txt")
+    rows = [tuple(int(v) for v in ln.split()) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return {lv: {r[1:] for r in rows if r[0] == lv} for lv in range(4)}
+
+
+def _expected_rank_for(blocks, L, l, tau, nu, sx, sw):
+    # block (tau, nu) at level l: space node at depth l, frequency node at height l (leaf units)
+    key = (nu << l, (nu + 1) << l, tau << (L - l), (tau + 1) << (L - l))
+    assert key in blocks, f"level {l} block (tau={tau}, nu={nu}) is not one the figure draws"
+    fl, fh, sl, sh = key
+    return min((sh - sl) * sx, (fh - fl) * sw)
+
+
+def test_level_structure_matches_the_papers_figure():
+    G = _figure_blocks()
+    for lv, blocks in G.items():  # every level tiles the 8 x 8 leaf grid with 8 equal blocks
+        cover = np.zeros((8, 8), dtype=int)
+        for fl, fh, sl, sh in blocks:
+            cover[sl:sh, fl:fh] += 1
+        assert len(blocks) == 8 and (cover == 1).all()
+        assert len({(fh - fl) * (sh - sl) for fl, fh, sl, sh in blocks}) == 1
+    # a Gaussian Phi with unequal leaf sizes (n = 8 * 32 points, m = 8 * 8 modes): the ID rank of
+    # every block is min(|tau|, |nu|), which tells which space node meets which frequency node
+    sx, sw, L = 32, 8, 3
+    n, m = 8 * sx, 8 * sw
+    Phi = np.random.default_rng(7).standard_normal((n, m))
+    space = (np.arange(n), np.arange(0, n + 1, sx))
+    F = B.build(B.dense_evaluator(Phi), n, m, np.arange(m, dtype=float), np.zeros((n, 3)), 1e-12, sx,
+                space=space)
+    assert F.L == L
+    for l in range(L + 1):
+        nb = 1 << (L - l)
+        for tau in range(1 << l):
+            for nu in range(nb):
+                assert F.ranks[l][tau * nb + nu] == _expected_rank_for(G[l], L, l, tau, nu, sx, sw)
