@@ -9,6 +9,7 @@
 // absolute (level 0 composes the frequency-tree permutation, levels >= 1 add the offset of
 // the input pair), so kernels gather without further indirection.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 
 #include "internal.h"
@@ -71,7 +72,10 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
   for (int l = 0; l <= L; ++l)
     for (int64_t b = 0; b < nb; ++b) off[l][b + 1] = off[l][b] + F.lv[l][b].r;
   P.vec_off.assign(L + 2, 0);
-  for (int l = 0; l <= L; ++l) P.vec_off[l + 1] = P.vec_off[l] + off[l][nb];
+  for (int l = 0; l <= L; ++l) {
+    if (off[l][nb] > INT32_MAX) fail(MHT_ERR_UNSUPPORTED, "a butterfly level has more than 2^31 - 1 entries");
+    P.vec_off[l + 1] = P.vec_off[l] + off[l][nb];
+  }
   P.vec_entries = P.vec_off[L + 1];
 
   // descriptors for both directions; matrix element offsets run synthesis data first
@@ -90,6 +94,7 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
         const Block& B = F.lv[s][b];
         d.rows = B.r;
         d.cols = B.K - B.r;
+        if (ient + B.K > INT32_MAX) fail(MHT_ERR_UNSUPPORTED, "more than 2^31 - 1 interpolation indices");
         d.idx_off = int(ient);
         d.out_off = int(off[s][b]);
         d.in_off = (s == 0) ? int(F.mode_off[b]) : int(off[s - 1][F.pair_index(s, b)]);
