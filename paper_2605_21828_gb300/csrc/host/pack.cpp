@@ -317,6 +317,93 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
     if (fp64) reinterpret_cast<double*>(img + P.weights_off)[i] = w;
     else reinterpret_cast<float*>(img + P.weights_off)[i] = float(w);
   }
+  validate_packed(P, F.n, F.m);
+}
+
+// Every address the apply kernels form from the image must stay inside its buffer; this
+// replays their accesses (the table above the row kernel: matrix rows, gathered indices,
+// output positions, permutation entries, work-item row ranges) on the host.
+void validate_packed(const Packed& P, int64_t n, int64_t m) {
+  auto bad = [](const char* what) { fail(MHT_ERR_FORMAT, std::string("packed plan: ") + what); };
+  const size_t isz = P.image.size();
+  const int L = P.L;
+  const int64_t nb = P.nb, es = P.elem_bytes;
+  if (int(P.st.size()) != L + 2 || int(P.vec_off.size()) != L + 2) bad("stage count");
+  for (int l = 0; l <= L; ++l)
+    if (P.vec_off[l + 1] < P.vec_off[l]) bad("level vector offsets");
+  auto len = [&](int l) { return P.vec_off[l + 1] - P.vec_off[l]; };
+  if (P.index_off < P.data_off || P.index_off + size_t(P.index_entries) * 4 > isz) bad("index region");
+  if (P.perm_off + size_t(n) * 4 > isz) bad("permutation region");
+  const int32_t* idx = reinterpret_cast<const int32_t*>(P.image.data() + P.index_off);
+  const int32_t* perm = reinterpret_cast<const int32_t*>(P.image.data() + P.perm_off);
+  {
+    std::vector<uint8_t> seen(size_t(n), 0);
+    for (int64_t i = 0; i < n; ++i) {
+      if (perm[i] < 0 || perm[i] >= n || seen[size_t(perm[i])]) bad("space permutation");
+      seen[size_t(perm[i])] = 1;
+    }
+  }
+  auto desc_at = [&](int dir, int s) {
+    const size_t off = P.st[s].dir[dir].desc_off;
+    if (off + size_t(nb) * sizeof(MhtBlockDesc) > isz) bad("descriptor region");
+    return reinterpret_cast<const MhtBlockDesc*>(P.image.data() + off);
+  };
+  for (int dir = 0; dir < 2; ++dir)
+    for (int s = 0; s <= L + 1; ++s) {
+      const MhtBlockDesc* D = desc_at(dir, s);
+      for (int64_t b = 0; b < nb; ++b) {
+        const MhtBlockDesc& d = D[b];
+        if (d.rows < 0 || d.cols < 0 || d.ldt < d.cols || (int64_t(d.ldt) * es) % 16 != 0 || d.t_off < 0 ||
+            (d.t_off * es) % 16 != 0 || size_t(d.t_off + int64_t(d.rows) * d.ldt) * es > P.index_off)
+          bad("matrix extent or alignment");
+        if (s <= L) {
+          const int64_t K = int64_t(d.rows) + d.cols;            // r + (K - r) in either direction
+          const int64_t r = dir == 0 ? d.rows : d.cols;
+          const int64_t in_len = s == 0 ? m : len(s - 1);
+          if (d.idx_off < 0 || d.idx_off + K > P.index_entries) bad("index list extent");
+          for (int64_t j = 0; j < K; ++j)
+            if (idx[d.idx_off + j] < 0 || idx[d.idx_off + j] >= in_len) bad("gathered index out of range");
+          if (d.out_off < 0 || d.out_off + r > len(s)) bad("output position out of range");
+          if (d.in_off < 0 || d.in_off + K > in_len) bad("input range");
+        } else {
+          const int64_t pts = dir == 0 ? d.rows : d.cols, rl = dir == 0 ? d.cols : d.rows;
+          if (d.out_off < 0 || d.out_off + pts > n) bad("space leaf range");
+          if (d.in_off < 0 || d.in_off + rl > len(L)) bad("level-L vector range");
+        }
+      }
+      auto check_items = [&](size_t off, int64_t count) {
+        if (off + size_t(count) * sizeof(MhtItem) > isz) bad("work-item region");
+        const MhtItem* it = reinterpret_cast<const MhtItem*>(P.image.data() + off);
+        for (int64_t k = 0; k < count; ++k) {
+          if (it[k].blk < 0 || it[k].blk >= nb || it[k].start < 0 || it[k].count < 0 || it[k].sib < 0 || it[k].sib > 1)
+            bad("work item");
+          const MhtBlockDesc& d = D[it[k].blk];
+          if (it[k].start + int64_t(it[k].count) > d.rows || (it[k].count == 0 && d.rows != 0))
+            bad("work-item rows");
+        }
+      };
+      check_items(P.st[s].dir[dir].items_off, P.st[s].dir[dir].nitems);
+      check_items(P.st[s].dir[dir].tc_items_off, P.st[s].dir[dir].tc_nitems);
+    }
+  for (int dir = 0; dir < 2; ++dir) {
+    const FusedDir& FD = P.fused[dir];
+    if (FD.items_off + size_t(FD.nitems) * sizeof(MhtPItem) > isz ||
+        FD.targets_off + size_t(L + 2) * nb * 4 > isz)
+      bad("persistent work-list region");
+    const MhtPItem* it = reinterpret_cast<const MhtPItem*>(P.image.data() + FD.items_off);
+    const int32_t* tgt = reinterpret_cast<const int32_t*>(P.image.data() + FD.targets_off);
+    std::vector<int32_t> per(size_t(L + 2) * nb, 0);
+    for (int64_t k = 0; k < FD.nitems; ++k) {
+      if (it[k].stage < 0 || it[k].stage > L + 1 || it[k].blk < 0 || it[k].blk >= nb || it[k].start < 0 ||
+          it[k].count < 0)
+        bad("persistent work item");
+      const MhtBlockDesc& d = desc_at(dir, it[k].stage)[it[k].blk];
+      if (it[k].start + int64_t(it[k].count) > d.rows) bad("persistent work-item rows");
+      ++per[size_t(it[k].stage) * nb + it[k].blk];
+    }
+    for (size_t k = 0; k < per.size(); ++k)
+      if (per[k] != tgt[k]) bad("completion targets");
+  }
 }
 
 }  // namespace mht
