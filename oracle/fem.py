@@ -65,47 +65,92 @@ def _m_orthonormalize(Phi: np.ndarray, Mdiag: np.ndarray) -> np.ndarray:
     return sla.solve_triangular(Lc, Phi.T, lower=True).T
 
 
+def _nearest_pairs(K, M, Mdiag, sigma, k, rng, V=None):
+    """The k pairs of K phi = lambda M phi nearest sigma by shift-invert Lanczos; with V
+    (M-orthonormal columns spanning found eigenvectors) the operator acts on the
+    M-orthogonal complement of V, so those pairs are skipped."""
+    n = K.shape[0]
+    v0 = rng.standard_normal(n)
+    if V is None or V.shape[1] == 0:
+        lam, vec = spla.eigsh(K, k=k, M=M, sigma=sigma, which="LM", v0=v0, tol=1e-12)
+    else:
+        lu = spla.splu((K - sigma * M).tocsc())
+
+        def solve(x):
+            y = lu.solve(np.asarray(x, dtype=np.float64).ravel())
+            return y - V @ (V.T @ (Mdiag * y))
+
+        op = spla.LinearOperator((n, n), matvec=solve, dtype=np.float64)
+        v0 = v0 - V @ (V.T @ (Mdiag * v0))
+        lam, vec = spla.eigsh(K, k=k, M=M, sigma=sigma, which="LM", v0=v0, tol=1e-12, OPinv=op)
+    o = np.argsort(lam)
+    return lam[o], vec[:, o]
+
+
 def eigenpairs_sliced(K: sp.spmatrix, Mdiag: np.ndarray, m: int, per_slice: int = 512,
                       area: float | None = None, seed: int = 0):
     """Lowest m pairs by shift-invert Lanczos in spectral slices (large meshes).
 
-    Each slice asks for ``per_slice`` pairs nearest a shift sigma placed (by Weyl's law) at
-    the middle of the next band of eigenvalues; pairs are merged by eigenvalue, duplicates
-    at band edges are removed by M-orthogonality, and the result is M-orthonormalized.
+    The spectrum is covered from the bottom by slices that partition it:
+
+    * the first slice asks for the ``per_slice`` pairs nearest a shift just below zero; K is
+      positive semidefinite, so these are the lowest pairs;
+    * every later slice is centred half a band above the covered part, the band width taken
+      from Weyl's law N(lambda) ~ A lambda / (4 pi) at first and from the previous slice's
+      observed width after that;
+    * the pairs nearest a shift are a contiguous stretch of the spectrum, so a slice is used
+      only if its stretch reaches well below the covered boundary (otherwise the shift moves
+      down and the slice is recomputed); single-vector Lanczos can miss copies of a multiple
+      eigenvalue, so the slice is searched again on the M-orthogonal complement of what it
+      found until the nearest remaining eigenvalue lies outside the stretch;
+    * it contributes its eigenvalues from the boundary up to just below its top, where the
+      window could cut a degenerate cluster, and that point becomes the new boundary.
+
+    The result is M-orthonormalized.
     """
     n = K.shape[0]
     if area is None:
         area = float(Mdiag.sum())
+    k = min(per_slice, n - 2)
     M = sp.diags(Mdiag).tocsc()
     K = K.tocsc()
-    lam_all, vec_all = [], []
     rng = np.random.default_rng(seed)
-    have = 0
-    lo = 0.0
-    while have < m:
-        # Weyl: the count below lambda is about area * lambda / (4 pi)
-        width = per_slice * 4.0 * np.pi / area
-        sigma = lo + 0.5 * width - (1e-3 if lo == 0.0 else 0.0)
-        v0 = rng.standard_normal(n)
-        lam, vec = spla.eigsh(K, k=per_slice, M=M, sigma=sigma, which="LM", v0=v0, tol=1e-12)
-        o = np.argsort(lam)
-        lam, vec = lam[o], vec[:, o]
-        for j in range(len(lam)):
-            v = vec[:, j]
-            if vec_all:
-                B = np.stack(vec_all, axis=1)
-                coeff = B.T @ (Mdiag * v)
-                if np.max(np.abs(coeff)) > 0.5 * np.sqrt(v @ (Mdiag * v)):
-                    continue  # already found in an earlier slice
-            lam_all.append(lam[j])
-            vec_all.append(v)
-        have = sum(1 for x in lam_all if x <= lam[-1])
-        lo = lam[-1] - 0.1 * width
-        if len(lam_all) >= m + per_slice:
-            break
-    lam_all = np.array(lam_all)
+    width = k * 4.0 * np.pi / area
+    lam_parts, vec_parts = [], []
+    covered = None  # every eigenvalue below `covered` has been taken, none above it
+    found = 0
+    while found < m:
+        sigma = -1e-3 * width if covered is None else covered + 0.5 * width
+        for _ in range(30):
+            lam, vec = _nearest_pairs(K, M, Mdiag, sigma, k, rng)
+            if covered is None or lam[0] < covered - 0.05 * (lam[-1] - lam[0]):
+                break
+            sigma = covered + 0.5 * (sigma - covered)  # the stretch missed the boundary
+        else:
+            raise RuntimeError("spectral slicing could not reach the covered part of the spectrum")
+        radius = max(abs(lam[0] - sigma), abs(lam[-1] - sigma))
+        for _ in range(50):  # recover copies of multiple eigenvalues the first pass missed
+            V = _m_orthonormalize(vec, Mdiag)
+            extra_l, extra_v = _nearest_pairs(K, M, Mdiag, sigma, min(16, n - 2 - vec.shape[1]), rng, V)
+            inside = np.abs(extra_l - sigma) < radius * (1 - 1e-10)
+            if not inside.any():
+                break
+            lam = np.concatenate([lam, extra_l[inside]])
+            vec = np.concatenate([vec, extra_v[:, inside]], axis=1)
+            o = np.argsort(lam)
+            lam, vec = lam[o], vec[:, o]
+        else:
+            raise RuntimeError("spectral slicing kept finding new copies of multiple eigenvalues")
+        top = lam[-1] - 1e-8 * max(abs(lam[-1]), 1.0)
+        keep = lam < top if covered is None else (lam >= covered) & (lam < top)
+        lam_parts.append(lam[keep])
+        vec_parts.append(vec[:, keep])
+        found += int(keep.sum())
+        covered = top
+        width = lam[-1] - lam[0]
+    lam_all = np.concatenate(lam_parts)
     o = np.argsort(lam_all, kind="stable")[:m]
-    Phi = np.stack(vec_all, axis=1)[:, o]
+    Phi = np.concatenate(vec_parts, axis=1)[:, o]
     return lam_all[o], _m_orthonormalize(Phi, Mdiag)
 
 
