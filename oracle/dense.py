@@ -21,32 +21,6 @@ def analyze(Phi: np.ndarray, f: np.ndarray, w: np.ndarray | None = None) -> np.n
     return Phi.conj().T @ g
 
 
-def synthesize_rows(row_eval, c: np.ndarray, rows: np.ndarray, chunk: int = 64) -> np.ndarray:
-    """f(rows) = Phi(rows, :) c with Phi evaluated row block by row block (matrix-free).
-
-    ``row_eval(rows) -> (len(rows), m)`` returns rows of Phi.
-    """
-    rows = np.asarray(rows)
-    out = []
-    for s in range(0, len(rows), chunk):
-        out.append(row_eval(rows[s:s + chunk]) @ c)
-    return np.concatenate(out, axis=0)
-
-
-def analyze_columns(col_eval, f: np.ndarray, cols: np.ndarray, w: np.ndarray | None = None,
-                    chunk: int = 64) -> np.ndarray:
-    """c(cols) = Phi(:, cols)^H diag(w) f with Phi evaluated column block by block.
-
-    ``col_eval(cols) -> (n, len(cols))`` returns columns of Phi.
-    """
-    g = f if w is None else (w[:, None] * f if f.ndim == 2 else w * f)
-    cols = np.asarray(cols)
-    out = []
-    for s in range(0, len(cols), chunk):
-        out.append(col_eval(cols[s:s + chunk]).conj().T @ g)
-    return np.concatenate(out, axis=0)
-
-
 def inverse(Phi: np.ndarray, f: np.ndarray) -> np.ndarray:
     """The inverse transform c = argmin_c ||Phi c - f||_2 (Sec. 7.1, Eq. inverse-MHT), by the
     library least-squares routine (SVD-based), column by column for f (n, k)."""

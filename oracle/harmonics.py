@@ -81,8 +81,3 @@ def sphere_phi(points: np.ndarray, lmax: int, ncols: int | None = None) -> np.nd
             if j0 - mm < ncols:
                 out[:, j0 - mm] = root2 * p * np.sin(mm * lon)
     return out
-
-
-def sphere_degree(j) -> np.ndarray:
-    """Degree l of the degree-ordered index j."""
-    return np.floor(np.sqrt(np.asarray(j, dtype=np.float64))).astype(np.int64)
