@@ -327,6 +327,16 @@ def test_library_level_structure_matches_the_papers_figure(mht_lib):
             assert ranks[l, b] == _expected_rank_for(G[l], L, l, b // nb, b % nb, sx, sw)
 
 
+@pytest.mark.parametrize("n", [64, 100])
+def test_library_fiedler_tree_bisects_a_segment(mht_lib, n):
+    from tests.test_oracle_butterfly import _assert_quarters, _segment_points
+    x, X = _segment_points(n)
+    Phi = np.random.default_rng(1).standard_normal((n, 16))
+    e = _plan_cls().build(n=n, m=16, eigenvalues=np.arange(16.0), evaluator="dense", dense=Phi, points=X,
+                          eps=1e-6, levels=2, tree="fiedler").export()
+    _assert_quarters(x, e["space_perm"], e["space_offsets"])
+
+
 def test_clone_and_set_mode(mht_lib):
     from paper_2605_21828_gb300 import MhtError
     n = 256

@@ -76,6 +76,30 @@ def test_space_tree_fiedler_separates_clusters():
     assert left == set(range(40)) or left == set(range(40, 80))
 
 
+def _segment_points(n, seed=0):
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0.0, 10.0, n)
+    return x, np.stack([x, 1e-3 * rng.standard_normal(n), 1e-3 * rng.standard_normal(n)], axis=1)
+
+
+def _assert_quarters(x, perm, off):
+    # Algorithm 2 on evenly spaced points of a segment: the graph is a uniform path, whose
+    # Fiedler vector is monotone and changes sign at the middle, and each half is again a
+    # path with free ends, so depth 2 gives four equal, contiguous quarters
+    n = len(x)
+    assert np.array_equal(np.diff(off), [n // 4] * 4)
+    spans = sorted((x[perm[off[i]:off[i + 1]]].min(), x[perm[off[i]:off[i + 1]]].max()) for i in range(4))
+    for q, (lo, hi) in enumerate(spans):
+        assert np.isclose(lo, x[q * n // 4]) and np.isclose(hi, x[(q + 1) * n // 4 - 1])
+
+
+@pytest.mark.parametrize("n", [64, 100])
+def test_space_tree_fiedler_bisects_a_segment(n):
+    x, X = _segment_points(n)
+    perm, off = B.space_tree(X, 2, "fiedler")
+    _assert_quarters(x, perm, off)
+
+
 def test_space_tree_depth_and_nesting():
     X = W.fibonacci_points(300, seed=1)
     perm, off = B.space_tree(X, 3, "fiedler")
