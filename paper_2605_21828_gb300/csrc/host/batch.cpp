@@ -7,6 +7,7 @@
 // The counters (queue head, abort word, one completion counter per instance, direction and
 // phase) are zeroed before every launch.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 
 #include "internal.h"
@@ -152,6 +153,45 @@ void batch_init(mht_batch& B, mht_plan* const* plans, int count, const int64_t* 
   B.counter_bytes = align256((size_t(2) + nctr) * sizeof(unsigned));
   B.status_off = B.counters_off + B.counter_bytes;
   B.ws_bytes = B.status_off + 256;
+  batch_validate(B);
+}
+
+// The persistent batch kernel claims items in ticket (list) order and lets an item wait until
+// the completion counter of its dependency reaches the dependency's item count.  That ends
+// without co-residency only if every dependency's items come earlier in the list; this checks
+// it, with the counters' uniqueness and the wait counts, before anything reaches the GPU.
+void batch_validate(const mht_batch& B) {
+  auto bad = [](const char* what) { fail(MHT_ERR_FORMAT, std::string("batch layout: ") + what); };
+  for (int dir = 0; dir < 2; ++dir) {
+    const std::vector<MhtBatchRec>& R = B.recs[dir];
+    const std::vector<MhtBItem>& I = B.items[dir];
+    const size_t nr = R.size();
+    std::vector<int64_t> first(nr, INT64_MAX), last(nr, -1), count(nr, 0);
+    for (size_t k = 0; k < I.size(); ++k) {
+      const int r = I[k].rec;
+      if (r < 0 || size_t(r) >= nr) bad("item record out of range");
+      if ((I[k].count_sib & 0x7fffffff) > B.rows_max || I[k].start < 0 || I[k].blk < 0) bad("item rows");
+      first[size_t(r)] = std::min<int64_t>(first[size_t(r)], int64_t(k));
+      last[size_t(r)] = int64_t(k);
+      ++count[size_t(r)];
+    }
+    std::vector<int> rec_of(size_t(B.nctr), -1);
+    for (size_t r = 0; r < nr; ++r) {
+      const int c = R[r].done_ctr;
+      if (c < 0 || c >= B.nctr || rec_of[size_t(c)] != -1) bad("completion counters");
+      rec_of[size_t(c)] = int(r);
+    }
+    for (size_t r = 0; r < nr; ++r) {
+      if (R[r].wait_ctr < 0) {
+        if (R[r].wait_count != 0) bad("wait count without a dependency");
+        continue;
+      }
+      if (R[r].wait_ctr >= B.nctr || rec_of[size_t(R[r].wait_ctr)] < 0) bad("dependency counter");
+      const size_t d = size_t(rec_of[size_t(R[r].wait_ctr)]);
+      if (d == r || int64_t(R[r].wait_count) != count[d]) bad("wait count differs from the dependency's items");
+      if (count[r] > 0 && count[d] > 0 && last[d] >= first[r]) bad("a dependency's items follow its dependent's");
+    }
+  }
 }
 
 // Fills the device addresses of every record (after binding; c / f after set_io).

@@ -317,6 +317,8 @@ struct mht_batch {
 namespace mht {
 void batch_init(mht_batch& B, mht_plan* const* plans, int count, const int64_t* nrhs);
 void batch_fill_records(mht_batch& B);
+// Checks the dependency order of the batch work list (throws MHT_ERR_FORMAT).
+void batch_validate(const mht_batch& B);
 BatchLaunch batch_launch_desc(const mht_batch& B, int dir, bool weighted);
 // Tensor-core form of a batch: every instance's own per-stage apply (3xTF32 products from 16
 // real / 8 complex RHS) on 8 forked streams, captured once into a CUDA graph and replayed.
