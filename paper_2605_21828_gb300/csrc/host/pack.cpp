@@ -276,25 +276,31 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
     }
   };
   int32_t* idx = reinterpret_cast<int32_t*>(img + P.index_off);
-  for (int s = 0; s < nst; ++s)
-    for (int64_t b = 0; b < nb; ++b) {
-      const MhtBlockDesc& d = desc[0][s][b];
-      const MhtBlockDesc& dt = desc[1][s][b];
-      const double* src = (s <= L) ? F.lv[s][b].T.data() : F.U[b].data();
-      for (int64_t i = 0; i < d.rows; ++i)
-        for (int64_t j = 0; j < d.cols; ++j) {
-          const double* v = src + (i * d.cols + j) * W;
-          store(d.t_off, i, j, d.ldt, v, false);
-          store(dt.t_off, j, i, dt.ldt, v, true);
-        }
-      if (s <= L) {
-        const Block& B = F.lv[s][b];
-        for (int j = 0; j < B.K; ++j) {
-          const int64_t loc = B.perm[j];
-          idx[d.idx_off + j] = int32_t(s == 0 ? F.mode_perm[F.mode_off[b] + loc] : int64_t(d.in_off) + loc);
-        }
+  // every (stage, block) writes its own matrices and index list: blocks in parallel, each
+  // matrix and its transpose in 32 x 32 tiles
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t sb = 0; sb < int64_t(nst) * nb; ++sb) {
+    const int s = int(sb / nb);
+    const int64_t b = sb % nb;
+    const MhtBlockDesc& d = desc[0][s][b];
+    const MhtBlockDesc& dt = desc[1][s][b];
+    const double* src = (s <= L) ? F.lv[s][b].T.data() : F.U[b].data();
+    for (int64_t i0 = 0; i0 < d.rows; i0 += 32)
+      for (int64_t j0 = 0; j0 < d.cols; j0 += 32)
+        for (int64_t i = i0; i < std::min<int64_t>(i0 + 32, d.rows); ++i)
+          for (int64_t j = j0; j < std::min<int64_t>(j0 + 32, d.cols); ++j) {
+            const double* v = src + (i * d.cols + j) * W;
+            store(d.t_off, i, j, d.ldt, v, false);
+            store(dt.t_off, j, i, dt.ldt, v, true);
+          }
+    if (s <= L) {
+      const Block& B = F.lv[s][b];
+      for (int j = 0; j < B.K; ++j) {
+        const int64_t loc = B.perm[j];
+        idx[d.idx_off + j] = int32_t(s == 0 ? F.mode_perm[F.mode_off[b] + loc] : int64_t(d.in_off) + loc);
       }
     }
+  }
   for (int dir = 0; dir < 2; ++dir) {
     for (int s = 0; s < nst; ++s) {
       std::memcpy(img + P.st[s].dir[dir].desc_off, desc[dir][s].data(), size_t(nb) * sizeof(MhtBlockDesc));
