@@ -112,7 +112,7 @@ struct SphereEval : Evaluator {
       const int64_t mm = k - l * l - l;
       groups[mm < 0 ? -mm : mm].push_back({l, mm, j});
     }
-    std::vector<double> zr(nr), sr(nr), pmm(nr), p1(nr), p2(nr), p(nr), cosm(nr), sinm(nr);
+    std::vector<double> zr(nr), sr(nr), pmm(nr), p1(nr), p2(nr), cosm(nr), sinm(nr);
     for (int64_t i = 0; i < nr; ++i) {
       zr[i] = z[rows[i]];
       sr[i] = s[rows[i]];
@@ -154,7 +154,7 @@ struct SphereEval : Evaluator {
       // emit columns as the recurrence passes their degree
       std::sort(list.begin(), list.end());
       size_t next = 0;
-      auto emit = [&](int64_t l, const std::vector<double>& P) {
+      auto emit = [&](int64_t l, const double* P) {
         while (next < list.size() && list[next][0] == l) {
           const int64_t mm = list[next][1];
           double* o = out + list[next][2] * ld;
@@ -167,24 +167,26 @@ struct SphereEval : Evaluator {
           ++next;
         }
       };
-      emit(am, pmm);
+      emit(am, pmm.data());
       if (lmax == am) continue;
       const double a1 = std::sqrt(2.0 * am + 3.0);
       for (int64_t i = 0; i < nr; ++i) {
         p2[i] = pmm[i];
         p1[i] = a1 * zr[i] * pmm[i];
       }
-      emit(am + 1, p1);
+      emit(am + 1, p1.data());
+      // Pbar_{l-1} in *cur, Pbar_{l-2} in *prev; each step overwrites the older one in place
+      double* cur = p1.data();
+      double* prev = p2.data();
+      const double* z = zr.data();
       for (int64_t l = am + 2; l <= lmax; ++l) {
         const double dl = double(l), dm = double(am);
         const double a = std::sqrt((4.0 * dl * dl - 1.0) / (dl * dl - dm * dm));
         const double b = std::sqrt(((dl - 1) * (dl - 1) - dm * dm) / (4.0 * (dl - 1) * (dl - 1) - 1.0));
-        for (int64_t i = 0; i < nr; ++i) {
-          p[i] = a * (zr[i] * p1[i] - b * p2[i]);
-          p2[i] = p1[i];
-          p1[i] = p[i];
-        }
-        if (next < list.size() && list[next][0] == l) emit(l, p1);
+#pragma omp simd
+        for (int64_t i = 0; i < nr; ++i) prev[i] = a * (z[i] * cur[i] - b * prev[i]);
+        std::swap(cur, prev);
+        if (next < list.size() && list[next][0] == l) emit(l, cur);
       }
     }
   }
