@@ -52,10 +52,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--multi-rhs", type=int, default=64, help="extra measurement at this many RHS (0: off)")
-    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64", "torus_sweep"],
+    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64", "torus_sweep", "peaks"],
                     help="batch64: 64 ragged instances (torus / sphere / deformed sphere, n in [2000, 40000], "
                          "m = n/4, 1-128 RHS each) in one persistent launch per direction; torus_sweep: the flat-torus "
-                         "memory law (m = ceil(n/25), eps 1e-3 and 1e-6) with single-RHS apply times")
+                         "memory law (m = ceil(n/25), eps 1e-3 and 1e-6) with single-RHS apply times; peaks: "
+                         "the GEMM rates the multi-RHS rooflines divide by (TF32, FP32, FP64, BF16)")
     ap.add_argument("--plan-cache", default=os.environ.get("MHT_PLAN_CACHE", ""))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -680,6 +681,49 @@ def run_torus_sweep(args):
                       "points": points, "loglog_fit": fit}), flush=True)
 
 
+def run_peaks(args):
+    """Dense GEMM rates of this GPU for the rooflines of the multi-RHS forms, measured like the
+    bf16 peak beside them: torch.matmul of 8192^3 (2 N^3 flops) in each type, best of 10 (burst)
+    and back to back for 4 s (sustained), CUDA events.  TF32 = float32 inputs with TF32 tensor
+    cores allowed; FP32 = float32 with TF32 off (SIMT FMA); FP64 = double."""
+    import torch
+    dev = torch.device("cuda", 0)
+    out = {}
+    for name, dt, tf32, N in (("bf16", torch.bfloat16, False, 8192), ("tf32", torch.float32, True, 8192),
+                              ("fp32", torch.float32, False, 8192), ("fp64", torch.float64, False, 4096)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        torch.backends.cudnn.allow_tf32 = tf32
+        a = torch.randn(N, N, device=dev, dtype=dt)
+        b = torch.randn(N, N, device=dev, dtype=dt)
+        c = a @ b
+        torch.cuda.synchronize()
+        best = 1e30
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(10):
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        reps, t_end = 0, time.time() + 4.0
+        e0.record()
+        while time.time() < t_end:
+            torch.matmul(a, b, out=c)
+            reps += 1
+            if reps % 8 == 0:
+                torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        sus = e0.elapsed_time(e1) / reps
+        out[name] = {"N": N, "tflops_burst": 2 * N ** 3 / (best / 1e3) / 1e12,
+                     "tflops_sustained": 2 * N ** 3 / (sus / 1e3) / 1e12}
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = False
+    print(json.dumps({"metric": "dense GEMM peaks", "gpu": torch.cuda.get_device_name(dev), "torch": torch.__version__,
+                      "how": "torch.matmul N^3 (2 N^3 flops): best of 10 (burst), back to back for 4 s (sustained)",
+                      "peaks": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -688,6 +732,8 @@ def main():
         run_batch(args)
     elif args.workload == "torus_sweep":
         run_torus_sweep(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     else:
         run_ours(args)
 

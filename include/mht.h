@@ -308,25 +308,51 @@ mht_status mht_apply_launch_count(const mht_plan* plan, int64_t nrhs, int64_t* l
  * that runs where cudaMalloc is not allowed (for instance inside a framework that owns the
  * device memory, or a region that must not allocate).  The paper has no counterpart; this
  * is a deployment variant of the persistent synthesis for real FP32 plans.  Its scratch
- * (the per-level butterfly vectors, per-block completion counters, the work-queue head and a
- * status word) lives in a fixed array of MHT_NOALLOC_SCRATCH_BYTES inside this library, which
- * every GPU that loads the library reserves until the process exits; a plan that needs more
- * is rejected with MHT_ERR_UNSUPPORTED and a message that gives both sizes.  Nothing is
- * allocated: the caller passes factor_dev (the plan's packed factors on the device,
- * 256-byte aligned -- for instance the buffer given to mht_plan_bind_device), c_dev (m floats)
- * and f_dev (n floats).  The first call on a device looks up the array's address on that
- * device; make that call before any stream capture.  All calls share the one array, which
- * keeps the previous call's contents (the call clears the parts that must start at zero):
- * calls that overlap on the GPU -- on different streams or from different threads -- race and
- * give wrong results, so serialize them.  Asynchronous on `stream`. */
+ * (a status word, the per-level butterfly vectors, per-block completion counters and the
+ * work-queue head) lives in a fixed array of MHT_NOALLOC_SCRATCH_BYTES inside this library,
+ * which every GPU that loads the library reserves until the process exits; a plan that needs
+ * more is rejected with MHT_ERR_UNSUPPORTED and a message that gives both sizes, and FP64 or
+ * complex plans with MHT_ERR_UNSUPPORTED.  Nothing is allocated: the caller passes factor_dev
+ * (the plan's packed factors on the device, 256-byte aligned -- for instance the buffer given
+ * to mht_plan_bind_device), c_dev (m floats) and f_dev (n floats).  The first call on a device
+ * looks up the array's address on that device; make that call before any stream capture.  All
+ * calls share the one array, which keeps the previous call's contents (the call clears the
+ * counters and the queue head, which must start at zero): calls that overlap on the GPU -- on
+ * different streams or from different threads -- race and give wrong results, so serialize
+ * them.  The kernel's waits are bounded (2 s); a wait that gives up sets a bit of the array's
+ * status word (the bits of mht_plan_check), stops the launch and leaves f unspecified.  The
+ * word is sticky -- later calls abort at once while it is set -- until mht_noalloc_check
+ * reads and clears it.  Asynchronous on `stream`. */
 #define MHT_NOALLOC_SCRATCH_BYTES (16u << 20)
 mht_status mht_synthesize_noalloc(const mht_plan* plan, const void* factor_dev, const void* c_dev,
                                   void* f_dev, void* stream);
 
+/* Reads and clears the status word of mht_synthesize_noalloc's scratch array on the current
+ * device (synchronizes `stream`; allocates nothing).  Returns MHT_OK with *flags = 0 when every
+ * bounded wait of the no-alloc calls since the last check completed, else MHT_ERR_TIMEOUT with
+ * the bits (those of mht_plan_check) in *flags. */
+mht_status mht_noalloc_check(void* stream, int32_t* flags);
+
+/* Testing aid for the failure path of mht_synthesize_noalloc: hold != 0 raises the completion
+ * target of one leaf-stage block in the caller's factor image factor_dev to a count that is
+ * never reached, so that the next no-alloc call gives up its bounded dependency wait (2 s),
+ * stops every CTA and reports bit 8 through mht_noalloc_check, leaving the context usable;
+ * hold == 0 restores the value from the plan.  Synchronous on `stream`. */
+mht_status mht_noalloc_debug_hold(const mht_plan* plan, void* factor_dev, int32_t hold, void* stream);
+
 /* Reads and clears the device status word of the bound workspace (synchronizes `stream`).
- * Kernels set bit 0 when a bounded wait for a bulk copy gives up instead of spinning
- * forever; the affected outputs are then unspecified.  Returns MHT_OK with *flags = 0 when
- * every wait since the last check completed, MHT_ERR_TIMEOUT (and the flags) otherwise. */
+ * Every device wait of the apply kernels is bounded (2 s); one that gives up sets a bit and
+ * the outputs of that apply are unspecified.  ANY nonzero value means that; the bits say
+ * which wait gave up:
+ *   1  per-stage kernel: a bulk copy of factor rows did not arrive;
+ *   2  persistent all-stage kernel: a free copy slot or item-queue slot did not come;
+ *   4  persistent all-stage kernel: a chunk of factor rows or the staged input did not arrive;
+ *   8  persistent all-stage kernel: a dependency (completion counter of the previous stage);
+ *   16 persistent all-stage kernel: the next work item or a free input buffer did not come;
+ *   32 tensor-core kernel: completion of the block products (tensor-core MMAs).
+ * While the word is nonzero, the persistent kernels abort at once.  Returns MHT_OK with
+ * *flags = 0 when every wait since the last check completed, MHT_ERR_TIMEOUT (and the flags)
+ * otherwise. */
 mht_status mht_plan_check(mht_plan* plan, void* stream, int32_t* flags);
 
 /* Apply path: 0 = automatic (currently one launch per stage, the faster path on the

@@ -93,6 +93,8 @@ SIGNATURES = {
     "mht_apply_launch_count": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "mht_plan_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "mht_synthesize_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mht_noalloc_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "mht_noalloc_debug_hold": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "mht_plan_set_path": (C.c_int, [C.c_void_p, C.c_int32]),
     "mht_plan_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "mht_plan_clone": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -1124,12 +1125,18 @@ int device_status(void* status_dev, void* stream, unsigned* flags, std::string& 
 // the library until the process exits.  Host code must not pass the array's name to a
 // kernel (in host code it is a host-side stand-in); its device address is looked up once per
 // device with cudaGetSymbolAddress while that device is current.
+//
+// Layout of the array: [0, 256) the status word (sticky: set by a bounded wait that gave up,
+// cleared only by mht_noalloc_check), then the level vectors, then the completion counters
+// and the queue head (cleared by every call).
 #include <mutex>
 
 namespace mht {
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // MHT_NOALLOC_SCRATCH_BYTES
+constexpr size_t kNoAllocScratchBytes = size_t(MHT_NOALLOC_SCRATCH_BYTES);
+static_assert(kNoAllocScratchBytes == (size_t(16) << 20), "scratch size of the allocation-free synthesis");
+constexpr size_t kNoAllocStatusBytes = 256;  // the status word's slot at the start of the array
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_noalloc_mutex;
@@ -1137,7 +1144,31 @@ void* g_noalloc_addr[256] = {};
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Device address of the scratch array on the current device (looked up once per device).
+int noalloc_base(uint8_t** base, std::string& err) {
+  int dev = 0;
+  if (int rc = check(cudaGetDevice(&dev), err, "cudaGetDevice")) return rc;
+  if (dev < 0 || dev >= 256) {
+    err = "device ordinal out of range";
+    return MHT_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {  // set-up: once per device, with that device current
+    void* a = nullptr;
+    if (int rc = check(cudaGetSymbolAddress(&a, g_noalloc_scratch), err, "cudaGetSymbolAddress")) return rc;
+    g_noalloc_addr[dev] = a;
+  }
+  *base = static_cast<uint8_t*>(g_noalloc_addr[dev]);
+  return 0;
+}
+
 }  // namespace
+
+size_t noalloc_scratch_need(const Packed& P) {
+  const size_t ncnt = size_t(P.L + 2) * P.nb + 1;
+  return kNoAllocStatusBytes + align256(size_t(std::max<int64_t>(P.vec_entries, 1)) * sizeof(float)) +
+         align256(ncnt * sizeof(unsigned));
+}
 
 int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void* c, void* f, void* stream,
                              std::string& err) {
@@ -1148,7 +1179,7 @@ int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void
   const size_t ncnt = size_t(P.L + 2) * P.nb + 1;
   const size_t y_bytes = align256(size_t(std::max<int64_t>(P.vec_entries, 1)) * sizeof(float));
   const size_t cnt_bytes = align256(ncnt * sizeof(unsigned));
-  const size_t need = y_bytes + cnt_bytes + 256;
+  const size_t need = noalloc_scratch_need(P);
   if (need > kNoAllocScratchBytes) {
     err = "this plan needs " + std::to_string(need) + " bytes of scratch; the no-alloc entry point has " +
           std::to_string(kNoAllocScratchBytes);
@@ -1159,28 +1190,15 @@ int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void
     err = "the fused synthesis does not fit in shared memory for this plan";
     return MHT_ERR_UNSUPPORTED;
   }
-  int dev = 0;
-  if (int rc = check(cudaGetDevice(&dev), err, "cudaGetDevice")) return rc;
-  if (dev < 0 || dev >= 256) {
-    err = "device ordinal out of range";
-    return MHT_ERR_INVALID_ARG;
-  }
-  void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {  // set-up: once per device, with that device current
-      void* a = nullptr;
-      if (int rc = check(cudaGetSymbolAddress(&a, g_noalloc_scratch), err, "cudaGetSymbolAddress")) return rc;
-      g_noalloc_addr[dev] = a;
-    }
-    base = g_noalloc_addr[dev];
-  }
-  auto* scratch = static_cast<uint8_t*>(base);
-  unsigned* cnt = reinterpret_cast<unsigned*>(scratch + y_bytes);
-  unsigned* status = reinterpret_cast<unsigned*>(scratch + y_bytes + cnt_bytes);
+  uint8_t* scratch = nullptr;
+  if (int rc = noalloc_base(&scratch, err)) return rc;
+  unsigned* status = reinterpret_cast<unsigned*>(scratch);
+  float* y = reinterpret_cast<float*>(scratch + kNoAllocStatusBytes);
+  unsigned* cnt = reinterpret_cast<unsigned*>(scratch + kNoAllocStatusBytes + y_bytes);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the array keeps the previous call's contents: counters, queue head and status start at zero
-  if (int rc = check(cudaMemsetAsync(cnt, 0, cnt_bytes + 256, s), err, "scratch reset")) return rc;
+  // the array keeps the previous call's contents: counters and queue head start at zero (the
+  // status word is left for mht_noalloc_check)
+  if (int rc = check(cudaMemsetAsync(cnt, 0, cnt_bytes, s), err, "scratch reset")) return rc;
   const FusedDir& FD = P.fused[0];
   if (FD.nitems == 0) return 0;
   auto kern = k_fused<float, false, 1, 0>;
@@ -1204,7 +1222,7 @@ int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void
   p.fout = static_cast<float*>(f);
   p.ldc = 1;  // single right-hand side: leading dimensions are irrelevant
   p.ldf = 1;
-  p.Y = reinterpret_cast<float*>(scratch);
+  p.Y = y;
   p.A0 = nullptr;
   p.A1 = nullptr;
   p.done = cnt;
@@ -1219,6 +1237,25 @@ int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void
   const int grid = int(std::min<int64_t>(num_sms(), FD.nitems));
   kern<<<grid, kFusedThreads, smem, s>>>(p);
   return check(cudaGetLastError(), err, "no-alloc synthesis launch");
+}
+
+int noalloc_status(void* stream, unsigned* flags, std::string& err) {
+  uint8_t* scratch = nullptr;
+  if (int rc = noalloc_base(&scratch, err)) return rc;
+  return device_status(scratch, stream, flags, err);
+}
+
+int noalloc_debug_hold(const Packed& P, void* factor_dev, bool hold, void* stream, std::string& err) {
+  // completion target of block 0 of stage 0 in the synthesis work list (later stages wait for it)
+  int32_t v = 0;
+  const size_t off = P.fused[0].targets_off;
+  std::memcpy(&v, P.image.data() + off, sizeof(v));
+  if (hold) v = 0x7fffffff;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int rc = check(cudaMemcpyAsync(static_cast<uint8_t*>(factor_dev) + off, &v, sizeof(v), cudaMemcpyHostToDevice, s),
+                     err, "debug hold"))
+    return rc;
+  return check(cudaStreamSynchronize(s), err, "debug hold sync");
 }
 
 }  // namespace mht

@@ -434,6 +434,31 @@ mht_status mht_synthesize_noalloc(const mht_plan* plan, const void* factor_dev, 
   });
 }
 
+mht_status mht_noalloc_check(void* stream, int32_t* flags) {
+  return guarded([&]() -> mht_status {
+    if (!flags) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    std::string err;
+    unsigned f = 0;
+    if (int rc = mht::noalloc_status(stream, &f, err)) return set_error(mht_status(rc), err);
+    *flags = int32_t(f);
+    if (f) return set_error(MHT_ERR_TIMEOUT, "a bounded device wait of the no-alloc synthesis gave up (status flags " +
+                                                 std::to_string(f) + ")");
+    return MHT_OK;
+  });
+}
+
+mht_status mht_noalloc_debug_hold(const mht_plan* plan, void* factor_dev, int32_t hold, void* stream) {
+  return guarded([&]() -> mht_status {
+    if (!plan || !factor_dev) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");
+    if (plan->P.fp64 || plan->P.cplx) mht::fail(MHT_ERR_UNSUPPORTED, "the no-alloc synthesis serves real FP32 plans");
+    if (plan->P.fused[0].nitems == 0) mht::fail(MHT_ERR_INVALID_ARG, "the plan has no synthesis work items");
+    std::string err;
+    if (int rc = mht::noalloc_debug_hold(plan->P, factor_dev, hold != 0, stream, err))
+      return set_error(mht_status(rc), err);
+    return MHT_OK;
+  });
+}
+
 mht_status mht_plan_check(mht_plan* plan, void* stream, int32_t* flags) {
   return guarded([&]() -> mht_status {
     if (!plan || !flags) mht::fail(MHT_ERR_INVALID_ARG, "NULL argument");

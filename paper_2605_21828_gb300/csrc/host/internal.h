@@ -222,6 +222,12 @@ int tc_stage_launch(const TcLaunch& a, std::string& err);
 // Fused FP32 synthesis of one vector with scratch from a fixed library array (no allocation).
 int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void* c, void* f, void* stream,
                              std::string& err);
+// Bytes of the fixed scratch array a plan's no-alloc synthesis needs (status word included).
+size_t noalloc_scratch_need(const Packed& P);
+// Reads and clears the no-alloc status word on the current device; synchronizes the stream.
+int noalloc_status(void* stream, unsigned* flags, std::string& err);
+// Makes (hold) or undoes an unreachable completion target in the caller's factor image.
+int noalloc_debug_hold(const Packed& P, void* factor_dev, bool hold, void* stream, std::string& err);
 // Copies the device status word to *flags, clears it, and synchronizes the stream.
 int device_status(void* status_dev, void* stream, unsigned* flags, std::string& err);
 

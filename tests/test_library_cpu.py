@@ -417,3 +417,55 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(mht_lib):
     assert lib.mht_batch_autotune(h, None, None) == 9
     assert lib.mht_batch_debug_hold(h, 0, 0, 1, None) == 9
     assert lib.mht_batch_destroy(h) == 0
+
+
+def _full_rank_factors(L, cplx=False):
+    """A structurally valid butterfly with one point and one mode per leaf and full-rank IDs
+    (r = K at every level): no transfer entries, but level vectors that double per level, so
+    2^L (2^(L+1) - 1) butterfly-vector entries in all."""
+    nb = 1 << L
+    ranks, lp, r = [], [], 1
+    for lev in range(L + 1):
+        K = 1 if lev == 0 else 2 * r
+        r = K
+        ranks += [r] * nb
+        lp += list(range(K)) * nb
+    dt = np.complex128 if cplx else np.float64
+    return {"n": nb, "m": nb, "levels": L, "complex": cplx, "space_perm": np.arange(nb),
+            "space_offsets": np.arange(nb + 1), "mode_perm": np.arange(nb), "mode_offsets": np.arange(nb + 1),
+            "ranks": np.array(ranks, np.int32), "local_perm": np.array(lp, np.int32),
+            "transfer": np.zeros(0, dt), "column_bases": np.ones(nb * r, dt)}
+
+
+def test_noalloc_synthesis_rejects_what_its_fixed_scratch_cannot_serve(mht_lib):
+    """The allocation-free synthesis checks, before any CUDA call: plans whose scratch exceeds
+    the fixed array (message with both sizes), FP64 and complex plans, and plans whose fused
+    kernel does not fit in shared memory.  None of these touch a GPU."""
+    from paper_2605_21828_gb300 import Plan, _lib
+    lib = _lib.load()
+    fake = C.c_void_p(256)  # never dereferenced: every rejection happens on the host
+    assert "(16u << 20)" in open(os.path.join(ROOT, "include", "mht.h")).read()
+    big = Plan.from_factors(_full_rank_factors(11), mode="fp32")  # 2048 * 4095 vector entries
+    rc = lib.mht_synthesize_noalloc(big._h, fake, fake, fake, None)
+    msg = lib.mht_last_error().decode()
+    assert rc == 8, msg  # UNSUPPORTED
+    sizes = [int(x) for x in re.findall(r"\d+", msg)]
+    assert 16 << 20 in sizes and any(s > 16 << 20 for s in sizes), msg
+    for F, mode in ((_full_rank_factors(3), "fp64"), (_full_rank_factors(3, cplx=True), "fp32")):
+        p = Plan.from_factors(F, mode=mode)
+        assert lib.mht_synthesize_noalloc(p._h, fake, fake, fake, None) == 8
+        assert "real FP32" in lib.mht_last_error().decode()
+        assert lib.mht_noalloc_debug_hold(p._h, fake, 1, None) == 8
+    # one block whose single row is 60000 entries wide: no fused ring slot fits in shared memory
+    K = 60001
+    wide = {"n": 1, "m": K, "levels": 0, "complex": False, "space_perm": np.arange(1), "space_offsets": [0, 1],
+            "mode_perm": np.arange(K), "mode_offsets": [0, K], "ranks": np.array([1], np.int32),
+            "local_perm": np.arange(K, dtype=np.int32), "transfer": np.ones(K - 1), "column_bases": np.ones(1)}
+    p = Plan.from_factors(wide, mode="fp32")
+    assert lib.mht_synthesize_noalloc(p._h, fake, fake, fake, None) == 8
+    assert "shared memory" in lib.mht_last_error().decode()
+    # misaligned factors and NULL arguments
+    small = Plan.from_factors(_full_rank_factors(3), mode="fp32")
+    assert lib.mht_synthesize_noalloc(small._h, C.c_void_p(260), fake, fake, None) == 1
+    assert lib.mht_synthesize_noalloc(small._h, fake, None, fake, None) == 1
+    assert lib.mht_noalloc_check(None, None) == 1
