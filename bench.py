@@ -228,6 +228,113 @@ def get_plan(args, dist, rank):
     return plan, time.time() - t0, built
 
 
+MODES_MULTI = {
+    # mode: (kernel description, tensor products per useful product, tensor dtype)
+    "fp32": ("k_rowdot (SIMT FP32, Kahan-compensated)", 0, None),
+    "3xtf32": ("k_tcs (tcgen05 kind::tf32: two-way split, 3 products, FP32 accumulation)", 3, "tf32"),
+    "6xbf16": ("k_tcs (tcgen05 kind::f16 BF16: exact three-way split, 6 products, FP32 accumulation)", 6, "bf16"),
+}
+
+
+def tensor_peak_tflops(dtype, peaks):
+    """Dense tensor peak for a kernel timed inside a long step: the driver's sustained bf16 GEMM
+    rate, and for TF32 that rate times the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    bf16 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+    return bf16 if dtype == "bf16" else bf16 * 1.1 / 2.25
+
+
+def multi_rhs_measure(args, plan, dev, stream, world, step, K):
+    """The same step with --multi-rhs vectors: plain FP32 SIMT products against the split
+    tensor-core products (3xTF32, 6xBF16), each timed, with its error against the FP64 apply of
+    the same factors and, for the tensor-core forms, the roofline of the block-product kernel."""
+    import torch
+
+    import workloads as W
+    km = args.multi_rhs
+    m = plan.m
+    plan.set_path("auto")  # wide RHS counts take the per-stage kernels
+    C = torch.from_numpy(W.sphere_coefficients(m, km)).float().to(dev)
+    multi = {"nrhs": km}
+    outs = {}
+    L = plan.levels
+    stages = [plan.level_info(s) for s in range(L + 2)]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    for mode, (kdesc, prods, tdt) in MODES_MULTI.items():
+        plan.set_mode(mode)
+        tuned = plan.autotune(km) if not args.no_autotune else []
+        for _ in range(3):
+            step(C)
+        torch.cuda.synchronize()
+        reps = max(3, K // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            step(C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mms = e0.elapsed_time(e1) / reps
+        outs[mode] = (plan.synthesize_raw(C), step(C))
+        r = {"ms_per_step": mms, "transforms_per_s": world * km / (mms / 1e3), "kernels": kdesc}
+        if prods:
+            # per-stage times of the same steps; the stages the tensor cores ran
+            plan.profile(True)
+            for _ in range(reps):
+                step(C)
+            torch.cuda.synchronize()
+            sm, _ = plan.stage_times(0)
+            am, _ = plan.stage_times(1)
+            plan.profile(False)
+            tens = {(t["direction"], t["stage"]) for t in tuned if t["tensor"]} if tuned else \
+                {(d, s) for d in (0, 1) for s in range(L + 2)}
+            t_ms, flops, nbytes = 0.0, 0.0, 0.0
+            for d, times in ((0, sm), (1, am)):
+                for s in range(L + 2):
+                    if (d, s) not in tens:
+                        continue
+                    E = stages[s]["transfer_entries"]
+                    t_ms += times[s] / reps
+                    flops += 2.0 * E * km  # useful: one multiply-add per stored entry and RHS
+                    # stored entries once per launch, vectors (gathered in + written out) per RHS
+                    nbytes += 4.0 * E + km * (stages[s]["algorithmic_bytes"] - 4.0 * E)
+            tpk = tensor_peak_tflops(tdt, peaks)
+            achieved = flops / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+            bound = min(hbm * 1e9 * flops / max(nbytes, 1.0) / 1e12, tpk / prods)
+            r["stage_ms"] = {"synthesis": [round(x / reps, 5) for x in sm], "adjoint": [round(x / reps, 5) for x in am]}
+            r["roofline"] = {"bound": "hbm" if hbm * 1e9 * flops / max(nbytes, 1.0) / 1e12 < tpk / prods else "tensor",
+                             "kernel": "k_tcs (both directions, tensor-core stages)", "achieved": achieved,
+                             "peak": bound, "unit": "TFLOP/s (useful, 2 flop per stored entry and RHS)",
+                             "frac": achieved / bound if bound > 0 else 0.0,
+                             "tensor_peak_tflops": tpk, "tensor_frac": achieved * prods / tpk,
+                             "hbm_GBps": nbytes / (t_ms / 1e3) / 1e9 if t_ms > 0 else 0.0,
+                             "hbm_frac": nbytes / (t_ms / 1e3) / 1e9 / hbm if t_ms > 0 else 0.0,
+                             "kernel_ms_per_step": t_ms, "intensity_flop_per_byte": flops / max(nbytes, 1.0),
+                             "peak_source": "min(MEASURED_PEAKS.json hbm_gbs x intensity, sustained "
+                                            f"{'bf16' if tdt == 'bf16' else 'bf16 x 1.1/2.25 (TF32)'} tensor peak / "
+                                            f"{prods} products) (of measured)"}
+        multi[mode] = r
+    plan.set_mode("fp32")
+    for mode in ("3xtf32", "6xbf16"):
+        multi[f"speedup_{mode}_vs_fp32"] = multi["fp32"]["ms_per_step"] / multi[mode]["ms_per_step"]
+    if not args.no_accuracy:
+        # rounding error of every FP32 form against the FP64 apply of the same factors (max over
+        # RHS of the relative l2 error per RHS)
+        ref = plan.clone("fp64").bind(device=dev, max_nrhs=km)
+        C64 = C.double()
+        r_syn = ref.synthesize_raw(C64)
+        r_rt = ref.analyze_raw(r_syn, weighted=True)
+        torch.cuda.synchronize()
+        for mode in MODES_MULTI:
+            for i, (nm, r) in enumerate((("synthesis", r_syn), ("round_trip", r_rt))):
+                e = torch.linalg.norm(outs[mode][i].double() - r, dim=0) / torch.linalg.norm(r, dim=0)
+                multi[mode][f"rel_err_{nm}_vs_fp64"] = float(e.max())
+        ref.close()
+        del ref, r_syn, r_rt, C64
+        torch.cuda.empty_cache()
+    return multi
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -371,50 +478,7 @@ def run_ours(args):
     # against the 3xTF32 tensor-core products, with the relative difference of their results
     multi = None
     if args.multi_rhs and args.multi_rhs > 1:
-        km = args.multi_rhs
-        plan.set_path("auto")  # wide RHS counts take the per-stage kernels
-        C = torch.from_numpy(W.sphere_coefficients(m, km)).float().to(dev)
-        multi = {"nrhs": km}
-        outs = {}
-        for mode in ("fp32", "3xtf32"):
-            plan.set_mode(mode)
-            if not args.no_autotune:
-                plan.autotune(km)
-            for _ in range(3):
-                step(C)
-            torch.cuda.synchronize()
-            reps = max(3, K // 4)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                step(C)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            mms = e0.elapsed_time(e1) / reps
-            outs[mode] = (plan.synthesize_raw(C), step(C))
-            multi[mode] = {"ms_per_step": mms, "transforms_per_s": world * km / (mms / 1e3)}
-        plan.set_mode("fp32")
-        multi["fp32"]["kernels"] = "k_rowdot (SIMT FP32)"
-        multi["3xtf32"]["kernels"] = "k_tc3 (tcgen05 kind::tf32, 3 products per k-step)"
-        for i, nm in enumerate(("synthesis", "round_trip")):
-            a_, b_ = outs["fp32"][i].double(), outs["3xtf32"][i].double()
-            multi[f"rel_diff_{nm}"] = float(torch.linalg.norm(a_ - b_) / torch.linalg.norm(a_))
-        multi["speedup_3xtf32_vs_fp32"] = multi["fp32"]["ms_per_step"] / multi["3xtf32"]["ms_per_step"]
-        if not args.no_accuracy:
-            # rounding error of both FP32 forms against the FP64 apply of the same factors
-            # (max over RHS of the relative l2 error per RHS)
-            ref = plan.clone("fp64").bind(device=dev, max_nrhs=km)
-            C64 = C.double()
-            r_syn = ref.synthesize_raw(C64)
-            r_rt = ref.analyze_raw(r_syn, weighted=True)
-            torch.cuda.synchronize()
-            for mode in ("fp32", "3xtf32"):
-                for i, (nm, r) in enumerate((("synthesis", r_syn), ("round_trip", r_rt))):
-                    e = torch.linalg.norm(outs[mode][i].double() - r, dim=0) / torch.linalg.norm(r, dim=0)
-                    multi[mode][f"rel_err_{nm}_vs_fp64"] = float(e.max())
-            ref.close()
-            del ref, r_syn, r_rt, C64
-            torch.cuda.empty_cache()
+        multi = multi_rhs_measure(args, plan, dev, stream, world, step, K)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

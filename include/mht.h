@@ -17,7 +17,7 @@
  *    the ABI.  A failed apply leaves its outputs unspecified.
  *  - Element types.  A plan has a field (real/complex) and an apply mode:
  *      MHT_APPLY_FP64  -> vectors are double (real) or interleaved (re, im) double pairs;
- *      MHT_APPLY_FP32 / MHT_APPLY_3XTF32 -> float or interleaved float pairs.
+ *      MHT_APPLY_FP32 / MHT_APPLY_3XTF32 / MHT_APPLY_6XBF16 -> float or interleaved float pairs.
  *  - Vector layout: column-major.  c is m x nrhs with leading dimension ldc >= m (counted
  *    in elements, one complex value = one element); f is n x nrhs with ldf >= n.  Rows are
  *    in the caller's ORIGINAL point / mode order (the order the problem was given in).
@@ -60,9 +60,15 @@ typedef enum { MHT_REAL = 0, MHT_COMPLEX = 1 } mht_field;
 typedef enum {
   MHT_APPLY_FP64 = 0,  /* factors and vectors in double, FP64 arithmetic                */
   MHT_APPLY_FP32 = 1,  /* factors and vectors in float, FP32 SIMT arithmetic            */
-  MHT_APPLY_3XTF32 = 2 /* float data; multi-RHS block products split into three TF32
-                          tensor-core products with FP32 accumulation (hi*hi + hi*lo +
-                          lo*hi); single-RHS applies use the FP32 kernels              */
+  MHT_APPLY_3XTF32 = 2, /* float data; multi-RHS block products on the tensor cores with
+                           each operand split into two TF32 parts (22 of FP32's 24 bits) and
+                           three products (hi*hi + hi*lo + lo*hi), FP32 accumulation;
+                           single-RHS applies use the FP32 kernels                     */
+  MHT_APPLY_6XBF16 = 3  /* float data; multi-RHS block products on the tensor cores with
+                           each operand split exactly into three BF16 parts and the six
+                           products down to order 2^-16 (x0y0 + x0y1 + x1y0 + x0y2 + x1y1 +
+                           x2y0), FP32 accumulation: FP32 accuracy; single-RHS applies use
+                           the FP32 kernels                                             */
 } mht_apply_mode;
 
 typedef enum {
@@ -361,12 +367,13 @@ mht_status mht_plan_check(mht_plan* plan, void* stream, int32_t* flags);
  * the same result. */
 mht_status mht_plan_set_path(mht_plan* plan, int32_t path);
 
-/* Switches the arithmetic of later applies between MHT_APPLY_FP32 and MHT_APPLY_3XTF32 on a
- * plan whose factors are stored in float (both modes read the same packed image, so no
- * rebinding is needed).  MHT_ERR_INVALID_ARG for an FP64 plan or for MHT_APPLY_FP64, whose
+/* Switches the arithmetic of later applies between MHT_APPLY_FP32, MHT_APPLY_3XTF32 and
+ * MHT_APPLY_6XBF16 on a plan whose factors are stored in float (all read the same packed image,
+ * so no rebinding is needed).  MHT_ERR_INVALID_ARG for an FP64 plan or for MHT_APPLY_FP64, whose
  * storage precision differs.  The block products of the apply (Sec. 2) with a block of
- * vectors take the tensor-core path only in MHT_APPLY_3XTF32 and from 16 real (8 complex)
- * RHS on; complex products run as real products of twice the width. */
+ * vectors take the tensor-core path only in the two split modes and from 16 real (8 complex)
+ * RHS on: one persistent launch per stage, tiles of 128 rows x up to 64 accumulator columns
+ * fed by 2-D TMA tensor maps; complex products run as real products of twice the width. */
 mht_status mht_plan_set_mode(mht_plan* plan, mht_apply_mode mode);
 
 /* Autotuner: times the candidate launch configurations of every stage of both directions
@@ -422,10 +429,11 @@ mht_status mht_batch_set_io(mht_batch* batch, void* const* c_dev, const int64_t*
 mht_status mht_batch_synthesize(mht_batch* batch, void* stream);
 /* c_i = Phi_i^H W_i f_i (weighted != 0) or Phi_i^H f_i for every instance. */
 mht_status mht_batch_analyze(mht_batch* batch, int32_t weighted, void* stream);
-/* MHT_APPLY_FP32 (default): the persistent FP32 kernel above.  MHT_APPLY_3XTF32: every
- * instance runs its own per-stage apply (tcgen05 3xTF32 block products from 16 real / 8 complex
- * RHS on, FP32 kernels below that) on eight forked streams, all captured once into one CUDA graph
- * and replayed; results equal mht_synthesize / mht_analyze of each plan in MHT_APPLY_3XTF32. */
+/* MHT_APPLY_FP32 (default): the persistent FP32 kernel above.  MHT_APPLY_3XTF32 or
+ * MHT_APPLY_6XBF16: every instance runs its own per-stage apply (tcgen05 split block products
+ * from 16 real / 8 complex RHS on, FP32 kernels below that) on eight forked streams, all
+ * captured once into one CUDA graph and replayed; results equal mht_synthesize / mht_analyze of
+ * each plan in that mode. */
 mht_status mht_batch_set_mode(mht_batch* batch, mht_apply_mode mode);
 /* 1 (default): launches replay CUDA graphs; 0: plain stream launches (same work). */
 mht_status mht_batch_set_graph(mht_batch* batch, int32_t use_graph);

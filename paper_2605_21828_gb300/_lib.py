@@ -11,7 +11,7 @@ MHT_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CALLBACK", 4: "NUMERIC", 5: "CUDA",
           6: "FORMAT", 7: "TIMEOUT", 8: "UNSUPPORTED", 9: "NOT_BOUND"}
 REAL, COMPLEX = 0, 1
-APPLY_FP64, APPLY_FP32, APPLY_3XTF32 = 0, 1, 2
+APPLY_FP64, APPLY_FP32, APPLY_3XTF32, APPLY_6XBF16 = 0, 1, 2, 3
 TREE_AUTO, TREE_FIEDLER, TREE_RECT, TREE_PCA_MEDIAN, TREE_GIVEN = 0, 1, 2, 3, 4
 EVAL_CALLBACK, EVAL_TORUS, EVAL_SPHERE, EVAL_DENSE = 0, 1, 2, 3
 

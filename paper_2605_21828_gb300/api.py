@@ -18,7 +18,7 @@ import numpy as np
 
 from . import _lib as L
 
-_MODES = {"fp64": L.APPLY_FP64, "fp32": L.APPLY_FP32, "3xtf32": L.APPLY_3XTF32}
+_MODES = {"fp64": L.APPLY_FP64, "fp32": L.APPLY_FP32, "3xtf32": L.APPLY_3XTF32, "6xbf16": L.APPLY_6XBF16}
 _TREES = {"auto": L.TREE_AUTO, "fiedler": L.TREE_FIEDLER, "rect": L.TREE_RECT,
           "pca": L.TREE_PCA_MEDIAN, "given": L.TREE_GIVEN}
 _EVALS = {"torus": L.EVAL_TORUS, "sphere": L.EVAL_SPHERE, "dense": L.EVAL_DENSE}
@@ -260,7 +260,7 @@ class Plan:
         return self
 
     def set_mode(self, mode: str):
-        """'fp32' or '3xtf32' on a float plan (same packed factors, no rebinding)."""
+        """'fp32', '3xtf32' or '6xbf16' on a float plan (same packed factors, no rebinding)."""
         L.check(L.load().mht_plan_set_mode(self._h, _MODES[mode]))
         self.mode = mode
         return self
@@ -560,8 +560,8 @@ class Batch:
         return ms.value
 
     def set_mode(self, mode: str = "fp32"):
-        """'fp32': one persistent FP32 launch per direction; '3xtf32': a CUDA graph of each
-        instance's own apply with tensor-core block products for wide RHS counts."""
+        """'fp32': one persistent FP32 launch per direction; '3xtf32' / '6xbf16': a CUDA graph of
+        each instance's own apply with tensor-core block products for wide RHS counts."""
         L.check(L.load().mht_batch_set_mode(self._h, _MODES[mode]))
         return self
 

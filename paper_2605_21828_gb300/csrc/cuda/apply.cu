@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -786,7 +787,7 @@ int fused_dispatch(const Ctx& c, int rt, const void* in, long long ld_in, void* 
 }
 
 // ---- tensor-core stages (3xTF32, FP32 plans, at least 16 real or 8 complex RHS) ----------
-bool use_tc(const Ctx& c) { return c.mode == MHT_APPLY_3XTF32 && !c.P.fp64 && c.nrhs >= (c.P.cplx ? 8 : 16); }
+bool use_tc(const Ctx& c) { return tensor_mode(c.mode) && !c.P.fp64 && c.nrhs >= (c.P.cplx ? 8 : 16); }
 
 int tc_launch(const Ctx& c, int s, int dir, int mode, const void* in0, const void* in1, long long is_e,
               long long is_k, void* out0, void* out1, long long os_e, long long os_k, const void* w) {
@@ -810,6 +811,14 @@ int tc_launch(const Ctx& c, int s, int dir, int mode, const void* in0, const voi
   a.nrhs = c.nrhs;
   a.mode = mode;
   a.cplx = c.P.cplx ? 1 : 0;
+  a.bf16 = c.mode == MHT_APPLY_6XBF16 ? 1 : 0;
+  static const int drain_chunks = [] {
+    const char* e = std::getenv("MHT_TC_DRAIN_CHUNKS");
+    return e && std::atoi(e) == 1 ? 1 : 2;
+  }();
+  // the two-way TF32 split already spends most of the FP32 error budget: drain every chunk
+  a.drain_chunks = a.bf16 ? drain_chunks : 1;
+  a.tmaps = c.d.base + c.P.tmap_off + size_t(dir * (c.P.L + 2) + s) * c.P.nb * 128;
   a.status = status_ptr(c);
   a.stream = c.s;
   StageTimer timer(c.d.prof, dir, s, c.s);
@@ -892,7 +901,7 @@ int autotune(Ctx& c, DeviceView& dv, std::vector<TuneRecord>* report) {
   if (int rc = check(cudaMemsetAsync(dv.ws, 0, P.ws_counters_offset(dv.max_nrhs, c.F.n, c.F.m), c.s), c.err, "tune zero"))
     return rc;
   std::vector<StageCfg> cands;
-  const bool tc_ok = sizeof(R) == 4 && c.mode == MHT_APPLY_3XTF32;
+  const bool tc_ok = sizeof(R) == 4 && tensor_mode(c.mode);
   // single RHS (bandwidth-bound): the ring's slot size and depth and the resident CTAs;
   // several RHS (issue-bound): the RHS tile, a few ring depths and CTA counts
   auto add = [&](int rt, int kb, int ns, int ps) {
@@ -1092,6 +1101,16 @@ int device_upload(void* dst, const void* src, size_t bytes, void* stream, std::s
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (int rc = check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s), err, "factor upload")) return rc;
   return check(cudaStreamSynchronize(s), err, "factor upload sync");
+}
+
+bool tensor_mode(mht_apply_mode m) { return m == MHT_APPLY_3XTF32 || m == MHT_APPLY_6XBF16; }
+
+int device_upload_image(const Packed& P, void* base_dev, void* stream, std::string& err) {
+  if (int rc = device_upload(base_dev, P.image.data(), P.image.size(), stream, err)) return rc;
+  if (P.fp64 || P.tmap_bytes == 0) return 0;
+  std::vector<uint8_t> maps;
+  if (int rc = tc_encode_tmaps(P, base_dev, maps, err)) return rc;
+  return device_upload(static_cast<uint8_t*>(base_dev) + P.tmap_off, maps.data(), maps.size(), stream, err);
 }
 
 int device_copy_async(void* dst, const void* src, size_t bytes, int kind, void* stream, std::string& err) {

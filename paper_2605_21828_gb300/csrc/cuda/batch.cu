@@ -421,8 +421,8 @@ int batch_tc_run(mht_batch& B, int dir, bool weighted, void* stream, std::string
       cudaStream_t st = g->side[i % TcGroup::kStreams];
       void* c = reinterpret_cast<void*>(I.c);
       void* f = reinterpret_cast<void*>(I.f);
-      rc = dir == 0 ? apply_synthesize(I.shape, I.meta, dv, c, I.ldc, f, I.ldf, I.nrhs, false, MHT_APPLY_3XTF32, st, err)
-                    : apply_analyze(I.shape, I.meta, dv, f, I.ldf, c, I.ldc, I.nrhs, weighted, MHT_APPLY_3XTF32, st, err);
+      rc = dir == 0 ? apply_synthesize(I.shape, I.meta, dv, c, I.ldc, f, I.ldf, I.nrhs, false, B.mode, st, err)
+                    : apply_analyze(I.shape, I.meta, dv, f, I.ldf, c, I.ldc, I.nrhs, weighted, B.mode, st, err);
     }
     // join: the origin waits for every side stream
     for (int k = 0; k < TcGroup::kStreams && !rc; ++k) {

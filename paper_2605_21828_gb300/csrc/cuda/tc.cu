@@ -1,32 +1,47 @@
-// Multi-RHS block products on the 5th-generation tensor cores (tcgen05), 3xTF32.
+// Multi-RHS block products on the 5th-generation tensor cores (tcgen05) with FP32-accurate
+// split operands.
 //
-// With k right-hand sides every butterfly block product becomes a GEMM: M = rows of the
-// stored matrix (T~ or U, or their transposes for the adjoint), N = k, K = its columns.  FP32
-// accuracy on TF32 tensor cores comes from splitting both operands, x = hi + lo with
-// hi = tf32(x) and lo = tf32(x - hi), and accumulating hi*hi + hi*lo + lo*hi in FP32
-// (Markidis et al. 2018; Ootomo & Yokota 2022); the dropped lo*lo term is below FP32
-// rounding.
+// With k right-hand sides every butterfly block product (Sec. 2: y = [I | T~] P^T x, and the
+// column-basis products) becomes a GEMM: M = rows of the stored matrix (T~ or U, or their
+// transposes for the adjoint), N = k, K = its columns.  The tensor cores multiply low-precision
+// operands exactly and accumulate in FP32, so every FP32 operand is split into pieces and the
+// significant piece products are summed:
+//   * 6xBF16 (MHT_APPLY_6XBF16): x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0),
+//     x2 = x - x0 - x1 (exact: three 8-bit significands cover FP32's 24 bits), and
+//     a b ~ a0 b0 + (a0 b1 + a1 b0) + (a0 b2 + a1 b1 + a2 b0); the dropped terms are below
+//     2^-23 |a b|.
+//   * 3xTF32 (MHT_APPLY_3XTF32): x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (22 of 24
+//     bits), a b ~ hi hi + (hi lo + lo hi) (Markidis et al. 2018; Ootomo & Yokota 2022).
+// The piece products a_i b_j (i + j < P) all accumulate into one TMEM accumulator, issued
+// smallest order first (i + j = P - 1, ..., 0): the tensor core's rounding of the running sum is
+// then relative to small partial sums until the two leading products a_0 b_0 land last.
 //
-// One CTA (16 warps) computes a 128-row tile of one block for N right-hand sides:
-//   * K is streamed in chunks of 32.  The matrix rows (16-byte cp.async) and the gathered
-//     input entries (4-byte cp.async) arrive two chunks ahead in a raw ring; both are split into
-//     hi/lo and written to shared memory in the canonical no-swizzle K-major layout (core
-//     matrices of 8 rows x 16 bytes; 128 bytes between core matrices along K, 1024 along M/N).
-//   * One thread issues, per chunk, 4 x 3 tcgen05.mma.kind::tf32 (M = 128, K = 8 each): hi*hi
-//     into one 128 x N FP32 tensor-memory buffer, hi*lo + lo*hi into a second, both starting
-//     from zero, and commits them to the chunk's mbarrier.  A 2-stage shared-memory ring and
-//     two pairs of TMEM buffers let the loads of chunk c+1 overlap the MMAs of chunk c.
-//   * After a chunk's MMAs complete, every warp reads its rows of both buffers (tcgen05.ld;
-//     warp w owns TMEM lanes 32 (w % 4) .. + 31 = tile rows, and quarter w / 4 of the columns)
-//     and adds them to FP32 registers with round-to-nearest and Kahan compensation, so
-//     tensor-core accumulation never spans more than one chunk of K.
-//   * The epilogue adds the identity term of the interpolative decomposition and stores the row.
-// Every mbarrier wait is bounded in time; on timeout the kernel sets a status bit, skips the
-// remaining work, and still releases its tensor memory.
+// One persistent CTA per SM (608 threads) walks work units (128-row tile of one block x one
+// tile of N accumulator columns), sorted by K on the host, in a fixed stride:
+//   warp 0      TMA producer: 128 x 32 FP32 tiles of the stored matrix by 2-D tensor maps
+//               (one per block, 128-byte swizzle, out-of-range rows / columns read as zero)
+//               into a ring of raw slots;
+//   warp 1      allocates tensor memory; one thread issues the MMAs of a chunk (K = 32) into
+//               one of four TMEM accumulator buffers and commits them to mbarriers;
+//   warp 2      gathers the chunk's input entries (the level vector rows named by the block's
+//               index list, the index loaded a chunk ahead) with cp.async into raw B slots;
+//   warps 3-18  split the raw A and B tiles into the pieces' canonical K-major core-matrix
+//               layout (2 stages), then drain the accumulator of the chunk two back (tcgen05.ld;
+//               warp w owns TMEM lanes 32 (w % 4) .. and a quarter of the columns) into FP32
+//               registers with Kahan compensation, and write each unit's rows in the epilogue
+//               (identity term of the ID, weights, scatter).
+// Tensor-core accumulation never spans more than one chunk of 32 columns.  Every mbarrier wait
+// is bounded in time; on timeout the kernel sets status bit 32 and an abort flag, every role
+// leaves its loop, copies and MMAs still in flight are waited for, and the tensor memory is
+// released.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 #include <string>
 
 #include "../host/internal.h"
@@ -34,10 +49,13 @@
 namespace mht {
 namespace {
 
-constexpr int kTcThreads = 512;  // 16 warps: TMEM lane quadrant = warp % 4, column quarter = warp / 4
-constexpr int kTcDepth = 3;      // raw chunk slots: chunks c, c+1, c+2 in flight
-constexpr int kTcM = 128;   // tile rows = tensor-memory lanes
-constexpr int kTcK = 32;    // K per pipeline stage (TF32 elements)
+constexpr int kMathWarp0 = 3;      // warps 3 .. 18 split, drain and write
+constexpr int kMathWarps = 16;     // four groups of four consecutive warps: lane quadrant x column group
+constexpr int kTcThreads = 32 * (kMathWarp0 + kMathWarps);
+constexpr int kTmemBufs = 4;       // accumulator buffers (N columns each) in flight
+constexpr int kTcM = 128;          // tile rows = tensor-memory lanes
+constexpr int kTcK = 32;           // FP32 columns of K per chunk
+constexpr int kRawA = kTcM * kTcK * 4;  // one TMA box
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
 enum TcMode { TC_SYN_ID = 0, TC_ADJ_ID = 1, TC_SYN_U = 2, TC_ADJ_U = 3 };
@@ -47,6 +65,7 @@ struct TcParams {
   const int* idx;
   const MhtBlockDesc* desc;
   const MhtItem* items;
+  const CUtensorMap* tmaps;  // one per block of the stage (this direction)
   const int* perm;
   const float* wts;
   const float* in0;
@@ -55,140 +74,333 @@ struct TcParams {
   float* out0;
   float* out1;
   long long os_e, os_k;
-  int nrhs;
+  int nitems, ntiles, nrhs;
+  int vec;                    // input rows of the RHS tile are contiguous and 16-byte aligned
   unsigned* status;
 };
 
+// ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ unsigned sa(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
+}
+// The waiting thread may sleep (up to the hint, 0.1 ms) until the phase completes, instead of
+// spinning through issue slots the working warps need.
 __device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned ph) {
   unsigned ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-               : "=r"(ok)
-               : "r"(sa(b)), "r"(ph)
-               : "memory");
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(sa(b)), "r"(ph), "r"(100000u)
+      : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned ph) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+// Bounded wait: false when it gave up (time limit: sets the status bit and the abort flag)
+// or when another role already aborted.
+__device__ __forceinline__ bool waitb(uint64_t* b, unsigned ph, volatile int* abort_flag, unsigned* status) {
   if (mbar_try(b, ph)) return true;
   const unsigned long long t0 = gtimer();
   for (unsigned it = 1;; ++it) {
     if (mbar_try(b, ph)) return true;
-    if ((it & 255) == 0 && gtimer() - t0 > kTcWaitNs) return false;
+    if ((it & 3) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kTcWaitNs) {
+        atomicOr(status, 32u);
+        *abort_flag = 1;
+        return false;
+      }
+    }
   }
 }
-__device__ __forceinline__ float tf32_rna(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// Bounded wait that ignores the abort flag (clean-up of copies and MMAs in flight).
+__device__ __forceinline__ void wait_quiet(uint64_t* b, unsigned ph) {
+  if (mbar_try(b, ph)) return;
+  const unsigned long long t0 = gtimer();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(b, ph)) return;
+    if ((it & 3) == 0 && gtimer() - t0 > kTcWaitNs) return;
+  }
 }
-__device__ __forceinline__ void split(float x, float& hi, float& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - hi);
-}
-// shared-memory matrix descriptor: no swizzle, K-major
-__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
-  return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
-         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-__device__ __forceinline__ void mma_tf32(unsigned tmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          sa(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(sa(bar))
       : "memory");
 }
-
-// 16-byte (A rows) and 4-byte (gathered B entries) asynchronous global -> shared copies; a
-// source size of 0 zero-fills the destination without reading (the address stays valid).
+// 16-byte / 4-byte asynchronous global -> shared copies; a source size of 0 zero-fills the
+// destination without reading (the address stays valid).
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, unsigned src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa(dst)), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, unsigned src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa(dst)), "l"(src), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(sa(b)) : "memory");
+}
+// shared-memory matrix descriptor: no swizzle, K-major (LBO: next core matrix along K, SBO:
+// next 8-row group)
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+template <bool BF16>
+__device__ __forceinline__ void mma(unsigned tmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
+  if constexpr (BF16)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Starts reading K consecutive 32-bit TMEM columns of this warp's 32 lanes (one row per
+// thread) into v; the registers are written asynchronously and valid after tmem_wait(v).
+template <int K>
+__device__ __forceinline__ void tmem_ld(unsigned taddr, float (&v)[K]) {
+  static_assert(K == 4 || K == 8 || K == 16 || K == 32, "columns per read");
+  if constexpr (K == 32) {
+    tmem_ld<16>(taddr, *reinterpret_cast<float(*)[16]>(&v[0]));
+    tmem_ld<16>(taddr + 16, *reinterpret_cast<float(*)[16]>(&v[16]));
+  } else if constexpr (K == 4)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(taddr)
+                 : "memory");
+  else if constexpr (K == 8)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+  else
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+          "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+// Waits for this thread's TMEM reads; the registers are operands, so no use of them can be
+// scheduled before the wait.
+template <int K>
+__device__ __forceinline__ void tmem_wait(float (&v)[K]) {
+  if constexpr (K == 32) {
+    tmem_wait<16>(*reinterpret_cast<float(*)[16]>(&v[0]));
+    tmem_wait<16>(*reinterpret_cast<float(*)[16]>(&v[16]));
+  } else if constexpr (K == 4)
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3])::"memory");
+  else if constexpr (K == 8)
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7])::"memory");
+  else
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                   "+f"(v[15])::"memory");
 }
 
-// core-matrix byte offset of element group (row m, 4-column group c4) in a no-swizzle K-major
-// tile with 32 columns: 8 x 16-byte core matrices, 128 bytes apart along K, 1024 along M/N
-__device__ __forceinline__ int core_off(int m, int c4) { return (m >> 3) * 1024 + c4 * 128 + (m & 7) * 16; }
-// A element group q (0..1023) of a 128 x 32 chunk: 8 consecutive q are the 8 rows of one core
-// matrix (their 16-byte stores fill 128 contiguous bytes: no bank conflicts), and a warp's 32
-// groups read 64 contiguous bytes from each of 8 rows
-__device__ __forceinline__ int a_row(int q) { return (q >> 6) * 8 + (q & 7); }
-__device__ __forceinline__ int a_col4(int q) { return (q >> 3) & 7; }
-
-// C: complex factors and vectors.  The complex product y = A x is computed as one real
-// product: A's interleaved storage is a real matrix of 2K columns, and column n of B holds
-// (xr, -xi) for output n < N/2 (the real parts) and (xi, xr) for output N/2 + n (the imaginary
-// parts), so a tile of N accumulator columns carries N/2 complex right-hand sides.
-//
-// Pipeline per chunk c (32 columns of K): the raw rows of A for chunk c + 2 and the gathered
-// B entries are requested with cp.async into a 3-slot raw ring (each thread copies, and later
-// converts, only its own elements, so no barrier separates the copy from the conversion);
-// chunk c is split into TF32 hi / lo operand tiles (2 stages), one thread issues its 12 MMAs,
-// and meanwhile every warp drains chunk c - 1 from tensor memory: warp w reads quarter w / 4 of
-// the accumulator columns for TMEM lane quadrant w % 4.
-template <int MODE, int N, bool C>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
-  static_assert(N == 16 || N == 32 || N == 64, "RHS tile");
-  constexpr int W = C ? 2 : 1;
-  constexpr int NR = N / W;   // right-hand sides per tile
-  constexpr int H = N / 4;    // accumulator columns drained per warp (one quarter)
-  constexpr int A_BYTES = kTcM * kTcK * 4;
-  constexpr int B_BYTES = N * kTcK * 4;
-  constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  constexpr int NB = MODE == TC_ADJ_ID ? 2 : 1;  // raw B buffers (input and sibling)
-  constexpr int RAW = A_BYTES + NB * B_BYTES;
-  constexpr int NCOLS = 4 * N;  // two chunk buffers x (hi*hi sum, correction sum)
-  constexpr int BG = N * (kTcK / 4);  // 4-entry groups of a B chunk
-  extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm);       // [2]
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(sm + 64);
-  volatile int* flag = reinterpret_cast<volatile int*>(sm + 68);
-  int* ksrc = reinterpret_cast<int*>(sm + 128);            // [kTcDepth][kTcK]
-  float* kw = reinterpret_cast<float*>(sm + 512);          // [kTcDepth][kTcK]
-  unsigned char* stages = sm + 1024;                       // [2][STAGE]
-  unsigned char* raw = stages + 2 * STAGE;                 // [kTcDepth][RAW]
-
-  const MhtItem it = p.items[blockIdx.x];
-  const MhtBlockDesc d = p.desc[it.blk];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int r0 = blockIdx.y * NR;
-  const int nk = min(NR, p.nrhs - r0);
-  float* out = (MODE == TC_ADJ_ID && it.sib) ? p.out1 : p.out0;
-
-  if (MODE == TC_ADJ_ID && it.start == 0) {  // identity part of [I | T~] P^T: out[skel_j] = z_j
-    for (int e = tid; e < d.cols * nk; e += kTcThreads) {
-      const int j = e / nk, t = e % nk;
-      const long long a = (((long long)d.out_off + j) * p.is_e + (long long)(r0 + t) * p.is_k) * W;
-      const long long o = ((long long)p.idx[d.idx_off + j] * p.os_e + (long long)(r0 + t) * p.os_k) * W;
+// ---------------------------------------------------------------- operand splitting
+// Two FP32 values -> BF16 pieces, packed (element 0 in the low half, as it sits in memory).
+__device__ __forceinline__ unsigned bf16x2(float lo, float hi) {
+  unsigned d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ float bf_lo(unsigned d) { return __uint_as_float(d << 16); }
+__device__ __forceinline__ float bf_hi(unsigned d) { return __uint_as_float(d & 0xffff0000u); }
+// x = x0 + x1 + x2 exactly for 8 values; p[i] = piece i as four packed words
+__device__ __forceinline__ void split_bf16(const float (&x)[8], uint4 (&p)[3]) {
+  unsigned w[3][4];
 #pragma unroll
-      for (int c = 0; c < W; ++c) {
-        float v = p.in0[a + c];
-        if (p.in1) v += p.in1[a + c];
-        out[o + c] = v;
-      }
+  for (int j = 0; j < 4; ++j) {
+    float a = x[2 * j], b = x[2 * j + 1];
+    const unsigned p0 = bf16x2(a, b);
+    a -= bf_lo(p0);
+    b -= bf_hi(p0);
+    const unsigned p1 = bf16x2(a, b);
+    a -= bf_lo(p1);
+    b -= bf_hi(p1);
+    w[0][j] = p0;
+    w[1][j] = p1;
+    w[2][j] = bf16x2(a, b);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) p[i] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+// x = hi + lo (to 22 bits) for 8 values; p[i][h] = piece i, values 4h .. 4h+3
+__device__ __forceinline__ void split_tf32(const float (&x)[8], uint4 (&p)[2][2]) {
+  float h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    h[j] = tf32_rna(x[j]);
+    l[j] = tf32_rna(x[j] - h[j]);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    p[0][q] = make_uint4(__float_as_uint(h[4 * q]), __float_as_uint(h[4 * q + 1]), __float_as_uint(h[4 * q + 2]),
+                         __float_as_uint(h[4 * q + 3]));
+    p[1][q] = make_uint4(__float_as_uint(l[4 * q]), __float_as_uint(l[4 * q + 1]), __float_as_uint(l[4 * q + 2]),
+                         __float_as_uint(l[4 * q + 3]));
+  }
+}
+// Writes the pieces of 8 consecutive K values of operand row r (K offset 8 k8 within the chunk)
+// into the canonical no-swizzle K-major layout: core matrices of 8 rows x 16 bytes, 128 bytes
+// apart along K, SBO apart along rows; piece i of the operand starts at base + i * piece_bytes.
+template <bool BF16>
+__device__ __forceinline__ void put_pieces(unsigned char* base, int piece_bytes, int r, int k8, const float (&x)[8]) {
+  if constexpr (BF16) {
+    constexpr int SBO = kTcK * 2 / 16 * 128;  // 512
+    uint4 p[3];
+    split_bf16(x, p);
+    const int off = (r >> 3) * SBO + k8 * 128 + (r & 7) * 16;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) *reinterpret_cast<uint4*>(base + i * piece_bytes + off) = p[i];
+  } else {
+    constexpr int SBO = kTcK * 4 / 16 * 128;  // 1024
+    uint4 p[2][2];
+    split_tf32(x, p);
+    const int off = (r >> 3) * SBO + (2 * k8) * 128 + (r & 7) * 16;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      *reinterpret_cast<uint4*>(base + i * piece_bytes + off) = p[i][0];
+      *reinterpret_cast<uint4*>(base + i * piece_bytes + off + 128) = p[i][1];
     }
   }
-  if (it.count == 0) return;
+}
 
-  const int K = d.cols * W;  // real columns
-  const int nchunks = (K + kTcK - 1) / kTcK;
+struct Unit {
+  MhtItem it;
+  MhtBlockDesc d;
+  int r0;   // first right-hand side of the tile
+  int nk;   // right-hand sides in the tile
+  int nch;  // chunks of 32 FP32 columns (0: no stored columns)
+};
+
+template <int N, bool C>
+__device__ __forceinline__ Unit get_unit(const TcParams& p, int u) {
+  constexpr int NR = C ? N / 2 : N;
+  Unit x;
+  const int item = u / p.ntiles, rt = u % p.ntiles;
+  x.it = p.items[item];
+  x.d = p.desc[x.it.blk];
+  x.r0 = rt * NR;
+  x.nk = min(NR, p.nrhs - x.r0);
+  x.nch = x.it.count > 0 ? (x.d.cols * (C ? 2 : 1) + kTcK - 1) / kTcK : 0;
+  return x;
+}
+
+// Shared memory of one CTA: raw A slots, two split stages, raw B slots, weights, barriers.
+template <int MODE, int N, bool C, bool BF16>
+__host__ __device__ constexpr size_t tc_smem(int ra, int rb) {
+  constexpr int W = C ? 2 : 1;
+  constexpr int NP = BF16 ? 3 : 2;
+  constexpr int PE = BF16 ? 2 : 4;
+  constexpr int STAGE = NP * (kTcM * kTcK * PE + N * kTcK * PE);
+  constexpr int RAWB = (MODE == TC_ADJ_ID ? 2 : 1) * kTcK * (N / W) * W * 4;
+  return 1024 + size_t(ra) * kRawA + 2 * size_t(STAGE) + size_t(rb) * RAWB + size_t(rb) * kTcK * 4 + 8 * 8 * 4 +
+         8 * (4 + 2 * kTmemBufs) + 64;
+}
+constexpr size_t kTcMaxSmem = 227 * 1024;
+// Ring depths: as many raw A slots (TMA tiles in flight, up to 8) as fit beside four raw B
+// slots (fewer B slots, down to 2, before A drops below 3).
+template <int MODE, int N, bool C, bool BF16>
+__host__ __device__ constexpr int tc_ra() {
+  int ra = 8;
+  while (tc_smem<MODE, N, C, BF16>(ra, 4) > kTcMaxSmem && ra > 3) --ra;
+  return ra;
+}
+template <int MODE, int N, bool C, bool BF16>
+__host__ __device__ constexpr int tc_rb() {
+  int rb = 4;
+  while (tc_smem<MODE, N, C, BF16>(tc_ra<MODE, N, C, BF16>(), rb) > kTcMaxSmem && rb > 2) --rb;
+  return rb;
+}
+
+// BF16: 6xBF16 split (3 pieces); else 3xTF32 (2 pieces).  N accumulator columns (complex:
+// N / 2 right-hand sides, real parts then imaginary parts).
+template <int MODE, int N, bool C, bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
+  static_assert(N == 16 || N == 32 || N == 64, "accumulator tile");
+  constexpr int W = C ? 2 : 1;
+  constexpr int NR = N / W;
+  constexpr int NP = BF16 ? 3 : 2;          // pieces per operand
+  constexpr int PE = BF16 ? 2 : 4;          // bytes per piece element
+  constexpr int A_PIECE = kTcM * kTcK * PE;
+  constexpr int B_PIECE = N * kTcK * PE;
+  constexpr int STAGE = NP * (A_PIECE + B_PIECE);
+  constexpr int NB = MODE == TC_ADJ_ID ? 2 : 1;  // raw B buffers (input and sibling)
+  constexpr int RAWB = NB * kTcK * NR * W * 4;   // one chunk's gathered entries
+  constexpr int KW = kTcK / W;                   // input entries per chunk
+  constexpr int H = N / (kMathWarps / 4);        // accumulator columns per math thread
+  constexpr int KSTEP = BF16 ? 16 : 8;           // K of one MMA
+  constexpr int SBO = kTcK * PE / 16 * 128;
+  constexpr int NCOLS = kTmemBufs * N <= 64 ? 64 : kTmemBufs * N <= 128 ? 128 : 256;
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte aligned base (the 128-byte swizzle pattern repeats every 1024 bytes)
+  unsigned char* sm = smem_raw + ((1024 - (sa(smem_raw) & 1023)) & 1023);
+  constexpr int RA = tc_ra<MODE, N, C, BF16>(), RB = tc_rb<MODE, N, C, BF16>();
+  static_assert(tc_smem<MODE, N, C, BF16>(RA, RB) <= kTcMaxSmem, "shared memory of the tensor-core kernel");
+  unsigned char* rawA = sm;                                  // [RA][16 KB], 1024-aligned
+  unsigned char* stages = rawA + size_t(RA) * kRawA;         // [2][STAGE], 1024-aligned
+  unsigned char* rawB = stages + 2 * STAGE;                  // [RB][RAWB]
+  float* kw = reinterpret_cast<float*>(rawB + size_t(RB) * RAWB);  // [RB][32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(kw + RB * kTcK);
+  uint64_t* a_full = bars;           // [RA]
+  uint64_t* a_empty = a_full + 8;    // [RA]
+  uint64_t* b_full = a_empty + 8;    // [RB]
+  uint64_t* b_empty = b_full + 8;    // [RB]
+  uint64_t* s_full = b_empty + 8;    // [2] split stage written
+  uint64_t* mma_done = s_full + 2;   // [2] chunk's MMAs complete (split stage free)
+  uint64_t* t_full = mma_done + 2;   // [kTmemBufs] chunk's sums ready in TMEM buffer
+  uint64_t* t_empty = t_full + kTmemBufs;  // [kTmemBufs] TMEM buffer drained
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(t_empty + kTmemBufs);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nunits = p.nitems * p.ntiles;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&mbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&mbar[1])) : "memory");
+    for (int i = 0; i < RA; ++i) {
+      mbar_init(&a_full[i], 1);
+      mbar_init(&a_empty[i], kMathWarps);
+    }
+    for (int i = 0; i < RB; ++i) {
+      mbar_init(&b_full[i], 32);  // one gather warp's cp.async arrivals per chunk
+      mbar_init(&b_empty[i], kMathWarps);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s_full[i], kMathWarps);
+      mbar_init(&mma_done[i], 1);
+    }
+    for (int i = 0; i < kTmemBufs; ++i) {
+      mbar_init(&t_full[i], 1);
+      mbar_init(&t_empty[i], kMathWarps);
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *flag = 1;
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)), "n"(NCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -197,248 +409,430 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc3(TcParams p) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *tmem_slot;
-  // instruction descriptor: D = F32, A = B = TF32, both K-major, N >> 3, M >> 4
-  const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | (unsigned(N >> 3) << 17) | (unsigned(kTcM >> 4) << 24);
-  const int ldr = d.ldt * W;  // real row stride of A
+  long long a_issued = 0;  // producer: TMA loads issued
+  int mma_issued = 0;      // MMA thread: chunks committed
 
-  // warp 0: sources (and weights) of chunk x's 32 real columns into ring slot x % kTcDepth
-  auto sources = [&](int x) {
-    const int kr = x * kTcK + (tid & 31);
-    const int kk = kr / W;  // complex: real column kr is part kr & 1 of entry kr >> 1
-    int src = -1;
-    float w = 1.f;
-    if (kr < K) {
-      if (MODE == TC_SYN_ID) {
-        src = p.idx[d.idx_off + d.rows + kk];
-        if (p.wts) w = p.wts[src];  // leaf stage: diagonal scale of the coefficients
-      }
-      else if (MODE == TC_ADJ_ID) src = d.out_off + kk;
-      else if (MODE == TC_SYN_U) src = d.in_off + kk;
-      else {
-        src = p.perm[d.out_off + kk];
-        if (p.wts) w = p.wts[src];
-      }
-    }
-    ksrc[(x % kTcDepth) * kTcK + (tid & 31)] = src;
-    kw[(x % kTcDepth) * kTcK + (tid & 31)] = w;
-  };
-  // every thread: requests its elements of chunk x (A rows, gathered B entries) and commits
-  auto request = [&](int x) {
-    if (x < nchunks) {
-      unsigned char* rs = raw + (x % kTcDepth) * RAW;
-#pragma unroll
-      for (int u = 0; u < A_BYTES / 16 / kTcThreads; ++u) {
-        const int q = tid + kTcThreads * u;
-        const int m = a_row(q), c4 = a_col4(q), kr = x * kTcK + c4 * 4;
-        const bool ok = m < it.count && kr < ldr;
-        const float* src = ok ? p.data + (d.t_off + (long long)(it.start + m) * d.ldt) * W + kr : p.data;
-        cp_async16(rs + q * 16, src, ok ? 16u : 0u);
-      }
-      const int* ks = ksrc + (x % kTcDepth) * kTcK;
-      for (int g = tid; g < BG; g += kTcThreads) {
-        const int n = g % N, c4 = g / N;
-        const int rn = C ? (n < NR ? n : n - NR) : n;  // right-hand side of column n
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int kl = c4 * 4 + j;
-          const int src = ks[kl];
-          const bool ok = src >= 0 && rn < nk;
-          long long a = 0;
-          if (ok) {
-            a = ((long long)src * p.is_e + (long long)(r0 + rn) * p.is_k) * W;
-            if (C) a += (n < NR) ? (kl & 1) : 1 - (kl & 1);  // (xr, -xi) / (xi, xr): component
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const Unit x = get_unit<N, C>(p, u);
+        const CUtensorMap* map = p.tmaps + x.it.blk;
+        for (int c = 0; c < x.nch; ++c) {
+          const int s = int(a_issued % RA);
+          const unsigned ph = unsigned((a_issued / RA) & 1);
+          if (!waitb(&a_empty[s], ph ^ 1u, abort_flag, p.status)) {
+            ok = false;
+            break;
           }
-          // raw B layout [j][group]: a warp's copies of one j land in consecutive words
-          cp_async4(rs + A_BYTES + (j * BG + g) * 4, ok ? p.in0 + a : p.in0, ok ? 4u : 0u);
+          mbar_expect_tx(&a_full[s], kRawA);
+          tma_load_2d(rawA + size_t(s) * kRawA, map, c * kTcK, x.it.start, &a_full[s]);
+          ++a_issued;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      // instruction descriptor: D = F32, A = B = BF16 (kind::f16) or TF32, both K-major,
+      // M = 128, N columns
+      const unsigned idesc = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
+                             (unsigned(N >> 3) << 17) | (unsigned(kTcM >> 4) << 24);
+      int g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const Unit x = get_unit<N, C>(p, u);
+        for (int c = 0; c < x.nch; ++c, ++g) {
+          const int s = g & 1, b = g % kTmemBufs;
+          if (!waitb(&t_empty[b], unsigned((g / kTmemBufs) & 1) ^ 1u, abort_flag, p.status) ||
+              !waitb(&s_full[s], unsigned((g >> 1) & 1), abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned char* st = stages + s * STAGE;
+          const unsigned a0 = sa(st), b0 = sa(st + NP * A_PIECE);
+          const unsigned d = tmem + unsigned(b * N);
+          // piece products a_i b_j (i + j < NP) into one accumulator, smallest order first
+          // (i + j = NP - 1, ..., 0), so that the tensor core's rounding of the running sum is
+          // relative to small partial sums until the leading products a_0 b_0 land last
+          bool first = true;
+          // descriptor start addresses advance by (bytes >> 4) in their low field
+          const uint64_t da = smem_desc(a0, 128, SBO), db = smem_desc(b0, 128, SBO);
+#pragma unroll
+          for (int ord = NP - 1; ord >= 0; --ord)
+#pragma unroll
+            for (int kk = 0; kk < kTcK / KSTEP; ++kk)
+#pragma unroll
+              for (int i = 0; i <= ord; ++i) {
+                const int j = ord - i;
+                mma<BF16>(d, da + uint64_t((i * A_PIECE + kk * 256) >> 4), db + uint64_t((j * B_PIECE + kk * 256) >> 4),
+                          idesc, first ? 0u : 1u);
+                first = false;
+              }
+          // stage s may be overwritten once these MMAs complete; the chunk's sums are ready
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           sa(&mma_done[s]))
+                       : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           sa(&t_full[b]))
+                       : "memory");
+          mma_issued = g + 1;
+        }
+      }
+    }
+  } else if (warp < kMathWarp0) {
+    // ------------------------------------------------------------ input gather (cp.async)
+    // lane -> one input entry of the chunk (two lanes per entry for complex), whose index is
+    // loaded one chunk ahead of its copies
+    const bool vec = p.vec != 0;  // contiguous 16-byte aligned rows of the tile's RHS (host check)
+    // per-input weights: the leaf stage's scale of the coefficients, the adjoint's W f
+    const bool in_w = p.wts && (MODE == TC_SYN_ID || MODE == TC_ADJ_U);
+    constexpr int P = 32 / KW;  // lanes per entry
+    const int j = lane % KW, q = lane / KW;
+    int u = blockIdx.x, c = 0;
+    Unit x{};
+    auto seek = [&]() -> bool {  // the next unit (from u on) with stored columns
+      for (; u < nunits; u += gridDim.x) {
+        x = get_unit<N, C>(p, u);
+        if (x.nch > 0) return true;
+      }
+      return false;
+    };
+    auto advance = [&]() -> bool {
+      if (++c < x.nch) return true;
+      c = 0;
+      u += gridDim.x;
+      return seek();
+    };
+    // index of this lane's input entry in chunk (x, c); -1 outside the block
+    auto src_of = [&]() -> int {
+      const int kk = c * KW + j;
+      if (kk >= x.d.cols) return -1;
+      if (MODE == TC_SYN_ID) return p.idx[x.d.idx_off + x.d.rows + kk];
+      if (MODE == TC_ADJ_ID) return x.d.out_off + kk;
+      if (MODE == TC_SYN_U) return x.d.in_off + kk;
+      return p.perm[x.d.out_off + kk];
+    };
+    bool have = seek();
+    long long g = 0;
+    int src_next = have ? src_of() : -1;
+    bool ok = true;
+    while (have && ok) {
+      const int r0 = x.r0;
+      const int src = src_next;
+      have = advance();  // the next chunk; its index load is issued now
+      if (have) src_next = src_of();
+      const int s = int(g % RB);
+      if (!waitb(&b_empty[s], unsigned((g / RB) & 1) ^ 1u, abort_flag, p.status)) {
+        ok = false;
+        break;
+      }
+      unsigned char* rb = rawB + size_t(s) * RAWB;
+      if (in_w && q == 0) cp_async4(kw + s * kTcK + j, src >= 0 ? p.wts + src : p.wts, src >= 0 ? 4u : 0u);
+      if (vec) {
+        // the tile's right-hand sides r0 .. r0 + NR - 1 of entry src: N floats, 4 per copy (nrhs W
+        // is a multiple of 4, so a copy is wholly inside or wholly outside the RHS range)
+#pragma unroll
+        for (int v = q; v < N / 4; v += P) {
+          const bool okc = src >= 0 && (r0 + (v * 4) / W) < p.nrhs;
+          const long long a = okc ? ((long long)src * p.is_e + r0) * W + v * 4 : 0;
+          cp_async16(rb + (j * N + v * 4) * 4, p.in0 + a, okc ? 16u : 0u);
           if (NB == 2)
-            cp_async4(rs + A_BYTES + B_BYTES + (j * BG + g) * 4, (ok && p.in1) ? p.in1 + a : p.in0,
-                      (ok && p.in1) ? 4u : 0u);
+            cp_async16(rb + (KW * N + j * N + v * 4) * 4, (okc && p.in1) ? p.in1 + a : p.in0,
+                       (okc && p.in1) ? 16u : 0u);
+        }
+      } else {
+        for (int e = q; e < N; e += P) {
+          const int n = e / W, cc = e % W;
+          const bool okc = src >= 0 && r0 + n < p.nrhs;
+          const long long a = okc ? ((long long)src * p.is_e + (long long)(r0 + n) * p.is_k) * W + cc : 0;
+          cp_async4(rb + (j * N + e) * 4, p.in0 + a, okc ? 4u : 0u);
+          if (NB == 2)
+            cp_async4(rb + (KW * N + j * N + e) * 4, (okc && p.in1) ? p.in1 + a : p.in0, (okc && p.in1) ? 4u : 0u);
         }
       }
+      cp_async_arrive(&b_full[s]);
+      ++g;
     }
-    cp_async_commit();
-  };
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
+    // ------------------------------------------------------------ split, drain, epilogue
+    const int mw = warp - kMathWarp0;  // 0 .. kMathWarps - 1
+    const int mt = tid - 32 * kMathWarp0;
+    const int quad = warp & 3, quarter = mw >> 2;  // TMEM lane quadrant, column group
+    static_assert(kMathWarps % 4 == 0, "whole groups of four warps cover the 128 TMEM lanes");
+    const int row = quad * 32 + lane;  // TMEM lane = tile row of this thread
+    const bool in_w = p.wts && (MODE == TC_SYN_ID || MODE == TC_ADJ_U);
+    float acc[H], cmp[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) acc[j] = cmp[j] = 0.f;
+    // chunks converted but not yet drained (at most two): unit index << 1 | last chunk of its unit
+    int pq0 = 0, pq1 = 0, np = 0;
+    bool ok = true;
+    int g = 0, gdr = 0;  // chunks converted, chunks drained
 
-  // Kahan-compensated row sums of this thread's quarter of the accumulator columns
-  float acc[H], cmp[H];
+    // waits (lane 0) with the verdict shared by the warp
+    auto wwait = [&](uint64_t* b, unsigned ph) -> bool {
+      int r = 1;
+      if (lane == 0) r = waitb(b, ph, abort_flag, p.status) ? 1 : 0;
+      return __shfl_sync(0xffffffffu, r, 0) != 0;
+    };
+    // rows of a unit: acc (Kahan-compensated sums) + identity term / weights, to the output
+    auto epilogue = [&](const Unit& x) {
+      if (row < x.it.count) {
+        const int i = x.it.start + row;
+        long long dst;
+        float wrow = 1.f;
+        long long sidx = -1;
+        float wsk = 1.f;
+        if (MODE == TC_SYN_ID) {
+          dst = (long long)x.d.out_off + i;
+          sidx = p.idx[x.d.idx_off + i];
+          if (p.wts) wsk = p.wts[sidx];
+        } else if (MODE == TC_ADJ_ID) {
+          dst = p.idx[x.d.idx_off + x.d.cols + i];
+        } else if (MODE == TC_SYN_U) {
+          dst = p.perm[x.d.out_off + i];
+          if (p.wts) wrow = p.wts[dst];
+        } else {
+          dst = (long long)x.d.in_off + i;
+        }
+        // this thread's H columns are consecutive right-hand sides of one component
+        const int col0 = quarter * H;
+        const int cc = C ? col0 / NR : 0;  // complex: real parts, then imaginary parts
+        const int n0 = C ? col0 % NR : col0;
+        float* o = ((MODE == TC_ADJ_ID && x.it.sib) ? p.out1 : p.out0) +
+                   (dst * p.os_e + (long long)(x.r0 + n0) * p.os_k) * W + cc;
+        const long long ostep = p.os_k * W;
+        const float* ip = p.in0;  // identity term of the synthesis ID stage
+        if (MODE == TC_SYN_ID) ip += (sidx * p.is_e + (long long)(x.r0 + n0) * p.is_k) * W + cc;
+        const long long istep = p.is_k * W;
+        const int nv = min(H, x.nk - n0);
 #pragma unroll
-  for (int j = 0; j < H; ++j) acc[j] = cmp[j] = 0.f;
-  const int quarter = warp >> 2;
-  int issued = 0, drained = 0;
-  // waits for chunk j's MMAs and adds its sums to acc; frees stage and TMEM buffer j & 1
-  auto drain = [&](int j) {
-    if (tid == 0 && *flag && !mbar_wait(&mbar[j & 1], unsigned((j >> 1) & 1))) {
-      atomicOr(p.status, 32u);
-      *flag = 0;
-    }
-    __syncthreads();
-    if (*flag) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned base = tmem + (unsigned((warp & 3) * 32) << 16) + unsigned((j & 1) * 2 * N + quarter * H);
-#pragma unroll
-      for (int cb = 0; cb < H / 4; ++cb) {
-        unsigned r[4], q[4];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                     : "r"(base + cb * 4)
-                     : "memory");
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                     : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3])
-                     : "r"(base + N + cb * 4)
-                     : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int n = cb * 4 + jj;
-          const float y = (__uint_as_float(r[jj]) + __uint_as_float(q[jj])) - cmp[n];
-          const float t = acc[n] + y;
-          cmp[n] = (t - acc[n]) - y;
-          acc[n] = t;
+        for (int j = 0; j < H; ++j) {
+          if (j < nv) {
+            float v = acc[j] - cmp[j];
+            if (MODE == TC_SYN_ID) v += wsk * *ip;
+            if (MODE == TC_SYN_U) v *= wrow;
+            *o = v;
+          }
+          o += ostep;
+          ip += istep;
         }
       }
+#pragma unroll
+      for (int j = 0; j < H; ++j) acc[j] = cmp[j] = 0.f;
+    };
+    // drain of chunk gdr, first half: wait for its sums and start reading this thread's H
+    // columns of its TMEM buffer (the read completes in drain_finish)
+    auto drain_start = [&](float (&d)[H]) -> bool {
+      const int b = gdr % kTmemBufs;
+      if (!wwait(&t_full[b], unsigned((gdr / kTmemBufs) & 1))) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tmem_ld<H>(tmem + (unsigned(quad * 32) << 16) + unsigned(b * N + quarter * H), d);
+      return true;
+    };
+    // second half: frees the buffer, adds the chunk into acc with Kahan compensation, and writes
+    // the unit's rows after its last chunk
+    auto drain_finish = [&](float (&d)[H], int entry) {
+      tmem_wait<H>(d);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    }
-    drained = j + 1;
-  };
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&t_empty[gdr % kTmemBufs]);
+      ++gdr;
+#pragma unroll
+      for (int n = 0; n < H; ++n) {
+        const float y = d[n] - cmp[n];
+        const float tt = acc[n] + y;
+        cmp[n] = (tt - acc[n]) - y;
+        acc[n] = tt;
+      }
+      if (entry & 1) epilogue(get_unit<N, C>(p, entry >> 1));
+    };
+    auto drain_one = [&](int entry) -> bool {
+      float d[H];
+      if (!drain_start(d)) return false;
+      drain_finish(d, entry);
+      return true;
+    };
+    // splits chunk c of unit x (global index gg) into stage gg & 1
+    auto convert = [&](const Unit& x, int c, int gg) -> bool {
+      const int sa_ = gg % RA, sb_ = gg % RB;
+      // the stage's previous chunk (gg - 2) must have been consumed by its MMAs
+      if (!wwait(&mma_done[gg & 1], unsigned((gg >> 1) & 1) ^ 1u)) return false;
+      if (!wwait(&a_full[sa_], unsigned((gg / RA) & 1)) || !wwait(&b_full[sb_], unsigned((gg / RB) & 1))) return false;
+      unsigned char* st = stages + (gg & 1) * STAGE;
+      // A: raw 128 x 32 FP32 tile, 128-byte rows, 16-byte chunk j of row r at position j ^ (r & 7)
+      const unsigned char* ra = rawA + size_t(sa_) * kRawA;
+#pragma unroll
+      for (int h2 = 0; h2 < 16 / kMathWarps; ++h2) {  // lane -> (row, 8-column group)
+        const int r = (mw + kMathWarps * h2) * 8 + (lane >> 2), k8 = lane & 3;
+        const float4 v0 = *reinterpret_cast<const float4*>(ra + r * 128 + (((2 * k8) ^ (r & 7)) << 4));
+        const float4 v1 = *reinterpret_cast<const float4*>(ra + r * 128 + (((2 * k8 + 1) ^ (r & 7)) << 4));
+        const float xv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        put_pieces<BF16>(st, A_PIECE, r, k8, xv);
+      }
+      // B': row n (accumulator column), K = 32 real columns
+      const float* rb = reinterpret_cast<const float*>(rawB + size_t(sb_) * RAWB);
+      const float* kws = kw + sb_ * kTcK;
+      for (int e = mt; e < 4 * N; e += 32 * kMathWarps) {
+        const int n = e % N, k8 = e / N;
+        float xv[8];
+        if (!C) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int k = k8 * 8 + j;
+            float v = rb[k * NR + n];
+            if (NB == 2) v += rb[KW * NR + k * NR + n];
+            if (in_w) v *= kws[k];
+            xv[j] = v;
+          }
+        } else {
+          const int rn = n < NR ? n : n - NR;  // right-hand side of this column
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int k = k8 * 4 + j;  // complex entry
+            float2 v = *reinterpret_cast<const float2*>(rb + (k * NR + rn) * 2);
+            if (NB == 2) {
+              const float2 v1 = *reinterpret_cast<const float2*>(rb + (KW * NR + k * NR + rn) * 2);
+              v.x += v1.x;
+              v.y += v1.y;
+            }
+            if (in_w) {
+              v.x *= kws[k];
+              v.y *= kws[k];
+            }
+            // columns (2k, 2k+1) of A's real view meet (xr, -xi) for real parts, (xi, xr) for imaginary
+            xv[2 * j] = n < NR ? v.x : v.y;
+            xv[2 * j + 1] = n < NR ? -v.y : v.x;
+          }
+        }
+        // piece j of B (N rows) sits at + j * B_PIECE
+        put_pieces<BF16>(st + NP * A_PIECE, B_PIECE, n, k8, xv);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&s_full[gg & 1]);
+        mbar_arrive(&a_empty[sa_]);
+        mbar_arrive(&b_empty[sb_]);
+      }
+      return true;
+    };
 
-  // prologue: sources of chunks 0..2, requests of chunks 0 and 1.  Afterwards the sources of
-  // chunk c+3 are written during iteration c ahead of drain(c-1)'s barrier, which publishes
-  // them before request(c+3) in the next iteration (two CTA barriers per chunk).
-  if (warp == 0)
-    for (int x = 0; x < kTcDepth && x < nchunks; ++x) sources(x);
-  __syncthreads();
-  for (int x = 0; x < kTcDepth - 1; ++x) request(x);
-  for (int c = 0; c < nchunks; ++c) {
-    const int s = c & 1;  // stage and TMEM buffer; chunk c-2 used them and was drained already
-    unsigned char* st = stages + s * STAGE;
-    unsigned char* Ahi = st;
-    unsigned char* Alo = st + A_BYTES;
-    unsigned char* Bhi = st + 2 * A_BYTES;
-    unsigned char* Blo = st + 2 * A_BYTES + B_BYTES;
-    request(c + kTcDepth - 1);
-    cp_async_wait<kTcDepth - 1>();  // this thread's copies of chunk c have landed
-    const unsigned char* rs = raw + (c % kTcDepth) * RAW;
-#pragma unroll
-    for (int u = 0; u < A_BYTES / 16 / kTcThreads; ++u) {
-      const int q = tid + kTcThreads * u;
-      const float4 v = *reinterpret_cast<const float4*>(rs + q * 16);
-      float4 h, l;
-      split(v.x, h.x, l.x);
-      split(v.y, h.y, l.y);
-      split(v.z, h.z, l.z);
-      split(v.w, h.w, l.w);
-      const int off = core_off(a_row(q), a_col4(q));
-      *reinterpret_cast<float4*>(Ahi + off) = h;
-      *reinterpret_cast<float4*>(Alo + off) = l;
-    }
-    const float* kwc = kw + (c % kTcDepth) * kTcK;
-    for (int g = tid; g < BG; g += kTcThreads) {
-      const int n = g % N, c4 = g / N;
-      const float* rb = reinterpret_cast<const float*>(rs + A_BYTES);
-      float x[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        x[j] = rb[j * BG + g];
-        if (NB == 2) x[j] += rb[BG * 4 + j * BG + g];  // sibling buffer (B_BYTES = 4 BG floats later)
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      const Unit x = get_unit<N, C>(p, u);
+      if (MODE == TC_ADJ_ID && x.it.start == 0) {
+        // identity part of [I | T~] P^T for this tile's right-hand sides: out[skel_j] = z_j
+        float* out = x.it.sib ? p.out1 : p.out0;
+        for (int e = mt; e < x.d.cols * x.nk * W; e += 32 * kMathWarps) {
+          const int j = e / (x.nk * W), q = e % (x.nk * W);
+          const long long rhs = x.r0 + q / W;
+          const int cc = q % W;
+          const long long a = (((long long)x.d.out_off + j) * p.is_e + rhs * p.is_k) * W + cc;
+          const long long o = ((long long)p.idx[x.d.idx_off + j] * p.os_e + rhs * p.os_k) * W + cc;
+          float v = p.in0[a];
+          if (p.in1) v += p.in1[a];
+          out[o] = v;
+        }
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        x[j] *= kwc[c4 * 4 + j];
-        if (C && n < NR && ((c4 * 4 + j) & 1)) x[j] = -x[j];  // (xr, -xi)
+      if (x.nch == 0) {  // no stored columns: drain what is pending, then the rows' identity terms
+        while (ok && np > 0) {
+          ok = drain_one(pq0);
+          pq0 = pq1;
+          --np;
+        }
+        if (!ok) break;
+        epilogue(x);
+        continue;
       }
-      float4 h, l;
-      split(x[0], h.x, l.x);
-      split(x[1], h.y, l.y);
-      split(x[2], h.z, l.z);
-      split(x[3], h.w, l.w);
-      const int off = core_off(n, c4);
-      *reinterpret_cast<float4*>(Bhi + off) = h;
-      *reinterpret_cast<float4*>(Blo + off) = l;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned dmain = tmem + unsigned(s * 2 * N), dcorr = dmain + N;
-#pragma unroll
-      for (int k8 = 0; k8 < kTcK / 8; ++k8) {
-        const uint64_t ah = smem_desc(sa(Ahi) + k8 * 256, 128, 1024);
-        const uint64_t al = smem_desc(sa(Alo) + k8 * 256, 128, 1024);
-        const uint64_t bh = smem_desc(sa(Bhi) + k8 * 256, 128, 1024);
-        const uint64_t bl = smem_desc(sa(Blo) + k8 * 256, 128, 1024);
-        mma_tf32(dmain, ah, bh, idesc, k8 > 0 ? 1u : 0u);
-        mma_tf32(dcorr, ah, bl, idesc, k8 > 0 ? 1u : 0u);
-        mma_tf32(dcorr, al, bh, idesc, 1u);
+      for (int c = 0; c < x.nch; ++c, ++g) {
+        // the chunk two back drains after this chunk's split; the previous chunk's MMAs run
+        // meanwhile
+        const bool dr = np == 2;
+        if (!(ok = convert(x, c, g))) break;
+        if (dr) {
+          float d[H];
+          if (!(ok = drain_start(d))) break;
+          drain_finish(d, pq0);
+          pq0 = pq1;
+          np = 1;
+        }
+        const int e = (u << 1) | (c == x.nch - 1 ? 1 : 0);
+        if (np == 0) pq0 = e;
+        else pq1 = e;
+        ++np;
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       sa(&mbar[s]))
-                   : "memory");
     }
-    issued = c + 1;
-    // sources of chunk c+3 into ring slot c % 3 (chunk c's weights were read before the last
-    // barrier, its requests long before)
-    if (warp == 0 && c + kTcDepth < nchunks) sources(c + kTcDepth);
-    if (c >= 1) drain(c - 1);  // overlaps the MMAs of chunk c; its barrier publishes the sources
-    else __syncthreads();
-    if (!*flag) break;
+    while (ok && np > 0) {
+      ok = drain_one(pq0);
+      pq0 = pq1;
+      --np;
+    }
   }
-  cp_async_wait<0>();  // no copy may still target shared memory when the CTA exits
-  if (issued > drained) drain(issued - 1);
-  // error path: committed MMAs must finish before tensor memory is released
-  if (tid == 0 && !*flag && issued > 0) mbar_wait(&mbar[(issued - 1) & 1], unsigned(((issued - 1) >> 1) & 1));
 
-  const int m = (warp & 3) * 32 + (tid & 31);  // TMEM lane = tile row
-  if (m < it.count) {
-    const int i = it.start + m;
-    long long dst;
-    float wrow = 1.f;
-    long long sidx = -1;
-    if (MODE == TC_SYN_ID) {
-      dst = (long long)d.out_off + i;
-      sidx = p.idx[d.idx_off + i];
-    } else if (MODE == TC_ADJ_ID) {
-      dst = p.idx[d.idx_off + d.cols + i];
-    } else if (MODE == TC_SYN_U) {
-      dst = p.perm[d.out_off + i];
-      if (p.wts) wrow = p.wts[dst];
-    } else {
-      dst = (long long)d.in_off + i;
-    }
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const int col = quarter * H + j;
-      const int c = C ? col / NR : 0;        // complex: real parts, then imaginary parts
-      const int n = C ? col % NR : col;      // right-hand side within the tile
-      if (n < nk) {
-        float v = acc[j] - cmp[j];
-        if (MODE == TC_SYN_ID)
-          v += (p.wts ? p.wts[sidx] : 1.f) * p.in0[(sidx * p.is_e + (long long)(r0 + n) * p.is_k) * W + c];
-        if (MODE == TC_SYN_U) v *= wrow;
-        out[(dst * p.os_e + (long long)(r0 + n) * p.os_k) * W + c] = v;
-      }
-    }
+  // ---------------------------------------------------------------- clean-up
+  __syncthreads();
+  if (*abort_flag) {
+    // copies and MMAs still in flight must land before shared and tensor memory are released
+    if (warp == 0 && lane == 0)
+      for (long long j = (a_issued > RA ? a_issued - RA : 0ll); j < a_issued; ++j)
+        wait_quiet(&a_full[j % RA], unsigned((j / RA) & 1));
+    if (warp == 1 && lane == 0 && mma_issued > 0)
+      wait_quiet(&mma_done[(mma_issued - 1) & 1], unsigned(((mma_issued - 1) >> 1) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOLS) : "memory");
+  }
 }
 
-template <int MODE, int N, bool C>
+
+template <int MODE, int N, bool C, bool BF16>
 int launch_n(const TcLaunch& a, std::string& err) {
-  constexpr int STAGE = 2 * kTcM * kTcK * 4 + 2 * N * kTcK * 4;
   constexpr int NR = C ? N / 2 : N;
-  constexpr int RAW = kTcM * kTcK * 4 + (MODE == TC_ADJ_ID ? 2 : 1) * N * kTcK * 4;
-  const size_t smem = 1024 + 2 * size_t(STAGE) + size_t(kTcDepth) * RAW;
-  auto kern = k_tc3<MODE, N, C>;
+  size_t smem = tc_smem<MODE, N, C, BF16>(tc_ra<MODE, N, C, BF16>(), tc_rb<MODE, N, C, BF16>());
+  // one CTA per SM: its tensor-memory allocation is sized for the whole SM's share
+  smem = std::max<size_t>(smem, 120 * 1024);
+  auto kern = k_tcs<MODE, N, C, BF16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) {
     err = std::string("tensor-core stage: ") + cudaGetErrorString(e);
     return MHT_ERR_CUDA;
   }
-  TcParams p{a.data, a.idx, a.desc, a.items, a.perm, a.wts, a.in0, a.in1, a.is_e, a.is_k,
-             a.out0, a.out1, a.os_e, a.os_k, int(a.nrhs), a.status};
-  dim3 grid(unsigned(a.nitems), unsigned((a.nrhs + NR - 1) / NR));
+  TcParams p{};
+  p.data = a.data;
+  p.idx = a.idx;
+  p.desc = a.desc;
+  p.items = a.items;
+  p.tmaps = static_cast<const CUtensorMap*>(a.tmaps);
+  p.perm = a.perm;
+  p.wts = a.wts;
+  p.in0 = a.in0;
+  p.in1 = a.in1;
+  p.is_e = a.is_e;
+  p.is_k = a.is_k;
+  p.out0 = a.out0;
+  p.out1 = a.out1;
+  p.os_e = a.os_e;
+  p.os_k = a.os_k;
+  p.nitems = int(a.nitems);
+  p.ntiles = int((a.nrhs + NR - 1) / NR);
+  p.nrhs = int(a.nrhs);
+  constexpr int W = C ? 2 : 1;
+  const auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  p.vec = (a.is_k == 1 && (a.is_e * W) % 4 == 0 && (a.nrhs * W) % 4 == 0 && al16(a.in0) && (!a.in1 || al16(a.in1)))
+              ? 1 : 0;
+  p.status = a.status;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long units = (long long)p.nitems * p.ntiles;
+  const int grid = int(std::min<long long>(std::max(sms, 1), units));
   kern<<<grid, kTcThreads, smem, static_cast<cudaStream_t>(a.stream)>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -449,30 +843,80 @@ int launch_n(const TcLaunch& a, std::string& err) {
 }
 
 // Accumulator tile: 16, 32 or 64 columns (complex: half as many right-hand sides); wider RHS
-// counts take several tiles across grid.y.
-template <int MODE, bool C>
+// counts take several tiles (work units).
+template <int MODE, bool C, bool BF16>
 int launch_mode(const TcLaunch& a, std::string& err) {
   const int64_t cols = a.nrhs * (C ? 2 : 1);
-  if (cols <= 16) return launch_n<MODE, 16, C>(a, err);
-  if (cols <= 32) return launch_n<MODE, 32, C>(a, err);
-  return launch_n<MODE, 64, C>(a, err);
+  if (cols <= 16) return launch_n<MODE, 16, C, BF16>(a, err);
+  if (cols <= 32) return launch_n<MODE, 32, C, BF16>(a, err);
+  return launch_n<MODE, 64, C, BF16>(a, err);
 }
 
-template <bool C>
+template <bool C, bool BF16>
 int launch_field(const TcLaunch& a, std::string& err) {
   switch (a.mode) {
-    case 0: return launch_mode<TC_SYN_ID, C>(a, err);
-    case 1: return launch_mode<TC_ADJ_ID, C>(a, err);
-    case 2: return launch_mode<TC_SYN_U, C>(a, err);
-    default: return launch_mode<TC_ADJ_U, C>(a, err);
+    case 0: return launch_mode<TC_SYN_ID, C, BF16>(a, err);
+    case 1: return launch_mode<TC_ADJ_ID, C, BF16>(a, err);
+    case 2: return launch_mode<TC_SYN_U, C, BF16>(a, err);
+    default: return launch_mode<TC_ADJ_U, C, BF16>(a, err);
   }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder(std::string& err) {
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f) {
+      err = "cuTensorMapEncodeTiled is not available from the driver";
+      return nullptr;
+    }
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
 }
 
 }  // namespace
 
 int tc_stage_launch(const TcLaunch& a, std::string& err) {
   if (a.nitems == 0) return 0;
-  return a.cplx ? launch_field<true>(a, err) : launch_field<false>(a, err);
+  if (a.bf16) return a.cplx ? launch_field<true, true>(a, err) : launch_field<false, true>(a, err);
+  return a.cplx ? launch_field<true, false>(a, err) : launch_field<false, false>(a, err);
+}
+
+// One 2-D tensor map per (direction, stage, block) of an FP32 image bound at `base_dev`: the
+// stored matrix as rows x (cols * W) FP32 with its padded row stride, boxes of 128 rows x 32
+// columns with the 128-byte swizzle; reads outside the matrix return zeros.
+int tc_encode_tmaps(const Packed& P, const void* base_dev, std::vector<uint8_t>& out, std::string& err) {
+  out.assign(P.tmap_bytes, 0);
+  if (P.fp64 || P.tmap_bytes == 0) return 0;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder(err);
+  if (!enc) return MHT_ERR_CUDA;
+  const int W = P.cplx ? 2 : 1;
+  const int nst = P.L + 2;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int s = 0; s < nst; ++s) {
+      const MhtBlockDesc* d = reinterpret_cast<const MhtBlockDesc*>(P.image.data() + P.st[s].dir[dir].desc_off);
+      for (int64_t b = 0; b < P.nb; ++b) {
+        CUtensorMap* m = reinterpret_cast<CUtensorMap*>(out.data() + size_t((dir * nst + s) * P.nb + b) * 128);
+        const uint8_t* addr = static_cast<const uint8_t*>(base_dev) + P.data_off + size_t(d[b].t_off) * W * 4;
+        const cuuint64_t dims[2] = {cuuint64_t(std::max(1, d[b].cols * W)), cuuint64_t(std::max(1, d[b].rows))};
+        const cuuint64_t strides[1] = {cuuint64_t(std::max(4, d[b].ldt * W)) * 4};
+        const cuuint32_t box[2] = {cuuint32_t(kTcK), cuuint32_t(kTcM)};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<uint8_t*>(addr), dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+          err = "cuTensorMapEncodeTiled failed (stage " + std::to_string(s) + ", block " + std::to_string(b) + ")";
+          return MHT_ERR_CUDA;
+        }
+      }
+    }
+  return 0;
 }
 
 }  // namespace mht

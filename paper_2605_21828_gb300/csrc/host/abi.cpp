@@ -36,7 +36,7 @@ mht_status guarded(Fn&& fn) {
 bool fp64_mode(mht_apply_mode m) { return m == MHT_APPLY_FP64; }
 
 void check_mode(mht_apply_mode m) {
-  if (m != MHT_APPLY_FP64 && m != MHT_APPLY_FP32 && m != MHT_APPLY_3XTF32)
+  if (m != MHT_APPLY_FP64 && m != MHT_APPLY_FP32 && m != MHT_APPLY_3XTF32 && m != MHT_APPLY_6XBF16)
     mht::fail(MHT_ERR_INVALID_ARG, "bad apply mode");
 }
 
@@ -262,8 +262,7 @@ mht_status mht_plan_bind_device(mht_plan* plan, void* factor_dev, size_t factor_
       mht::fail(MHT_ERR_OOM, "workspace buffer too small for max_nrhs");
     std::string err;
     plan->bound = false;
-    if (int rc = mht::device_upload(factor_dev, plan->P.image.data(), plan->P.image.size(), stream, err))
-      return set_error(mht_status(rc), err);
+    if (int rc = mht::device_upload_image(plan->P, factor_dev, stream, err)) return set_error(mht_status(rc), err);
     plan->dev.base = static_cast<const uint8_t*>(factor_dev);
     plan->dev.ws = static_cast<uint8_t*>(workspace_dev);
     plan->dev.ws_bytes = workspace_bytes;
@@ -485,8 +484,8 @@ mht_status mht_plan_set_path(mht_plan* plan, int32_t path) {
 mht_status mht_plan_set_mode(mht_plan* plan, mht_apply_mode mode) {
   return guarded([&]() -> mht_status {
     if (!plan) mht::fail(MHT_ERR_INVALID_ARG, "NULL plan");
-    if (plan->P.fp64 || (mode != MHT_APPLY_FP32 && mode != MHT_APPLY_3XTF32))
-      mht::fail(MHT_ERR_INVALID_ARG, "set_mode switches only between FP32 and 3XTF32 on a float plan");
+    if (plan->P.fp64 || (mode != MHT_APPLY_FP32 && !mht::tensor_mode(mode)))
+      mht::fail(MHT_ERR_INVALID_ARG, "set_mode switches only between FP32, 3XTF32 and 6XBF16 on a float plan");
     plan->mode = mode;
     return MHT_OK;
   });
@@ -665,7 +664,7 @@ mht_status mht_batch_bind_device(mht_batch* batch, void* image_dev, size_t image
     batch->ws_dev = static_cast<uint8_t*>(workspace_dev);
     std::string err;
     for (const mht::BatchInst& I : batch->inst)
-      if (int rc = mht::device_upload(batch->image_dev + I.image_off, I.plan->P.image.data(), I.image_bytes, stream, err))
+      if (int rc = mht::device_upload_image(I.plan->P, batch->image_dev + I.image_off, stream, err))
         mht::fail(mht_status(rc), err);
     for (int dir = 0; dir < 2; ++dir)
       if (int rc = mht::device_upload(batch->image_dev + batch->items_off[dir], batch->items[dir].data(),
@@ -725,7 +724,7 @@ static mht_status batch_run(mht_batch* batch, int dir, bool weighted, void* stre
   if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
   if (!batch->bound || !batch->io_set) mht::fail(MHT_ERR_NOT_BOUND, "batch is not bound or has no vectors");
   std::string err;
-  if (batch->mode == MHT_APPLY_3XTF32) {
+  if (mht::tensor_mode(batch->mode)) {
     if (int rc = mht::batch_tc_run(*batch, dir, weighted, stream, err)) mht::fail(mht_status(rc), err);
     return MHT_OK;
   }
@@ -753,7 +752,13 @@ mht_status mht_batch_analyze(mht_batch* batch, int32_t weighted, void* stream) {
 mht_status mht_batch_set_mode(mht_batch* batch, mht_apply_mode mode) {
   return guarded([&]() -> mht_status {
     if (!batch) mht::fail(MHT_ERR_INVALID_ARG, "NULL batch");
-    if (mode != MHT_APPLY_FP32 && mode != MHT_APPLY_3XTF32) mht::fail(MHT_ERR_INVALID_ARG, "FP32 or 3XTF32 only");
+    if (mode != MHT_APPLY_FP32 && !mht::tensor_mode(mode))
+      mht::fail(MHT_ERR_INVALID_ARG, "FP32, 3XTF32 or 6XBF16 only");
+    if (mode != batch->mode)
+      for (auto*& g : batch->tc) {  // the captured per-instance applies hold the arithmetic
+        mht::tc_group_destroy(g);
+        g = nullptr;
+      }
     batch->mode = mode;
     return MHT_OK;
   });

@@ -58,6 +58,8 @@ void batch_init(mht_batch& B, mht_plan* const* plans, int count, const int64_t* 
       M.perm_off = Q.perm_off;
       M.weights_off = Q.weights_off;
       M.vecoff_off = Q.vecoff_off;
+      M.tmap_off = Q.tmap_off;
+      M.tmap_bytes = Q.tmap_bytes;
       M.st = Q.st;
       M.fused[0] = Q.fused[0];
       M.fused[1] = Q.fused[1];

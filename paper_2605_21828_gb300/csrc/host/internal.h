@@ -123,6 +123,9 @@ struct Packed {
   int64_t nb = 0;
   std::vector<uint8_t> image;
   size_t data_off = 0, index_off = 0, perm_off = 0, weights_off = 0, vecoff_off = 0;
+  // tensor maps of the tensor-core stages: one 128-byte CUtensorMap per (direction, stage,
+  // block), encoded when the image is bound (they hold device addresses); FP32 images only
+  size_t tmap_off = 0, tmap_bytes = 0;
   std::vector<Stage> st;        // L+2 stages: ID levels 0..L, then U
   FusedDir fused[2];
   std::vector<int64_t> vec_off; // [L+2] offsets of the level vectors (per RHS), vec_off[L+1] = total
@@ -215,10 +218,18 @@ struct TcLaunch {
   int64_t nrhs;
   int mode;  // 0 synthesis ID stage, 1 adjoint ID stage, 2 synthesis column bases, 3 adjoint
   int cplx;  // complex factors and vectors (interleaved float pairs)
+  int bf16;  // 1: 6xBF16 split products, 0: 3xTF32
+  int drain_chunks = 2;  // chunks of 32 columns a tensor-memory accumulation spans (1 or 2)
+  const void* tmaps;  // the stage's tensor maps (one per block, this direction) in the image
   unsigned* status;
   void* stream;
 };
 int tc_stage_launch(const TcLaunch& a, std::string& err);
+// Tensor maps of an FP32 image bound at base_dev (P.tmap_bytes bytes, for [P.tmap_off]).
+int tc_encode_tmaps(const Packed& P, const void* base_dev, std::vector<uint8_t>& out, std::string& err);
+// Uploads the image to base_dev and, for FP32 plans, its tensor maps (synchronous).
+int device_upload_image(const Packed& P, void* base_dev, void* stream, std::string& err);
+bool tensor_mode(mht_apply_mode m);
 // Fused FP32 synthesis of one vector with scratch from a fixed library array (no allocation).
 int apply_synthesize_noalloc(const Packed& P, const void* factor_dev, const void* c, void* f, void* stream,
                              std::string& err);

@@ -198,6 +198,12 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
         for (int r0 = 0; r0 < d.rows; r0 += 128)
           tcitems[dir][s].push_back({int(b), r0, std::min(128, d.rows - r0), sib});
       }
+      // longest first (K columns stream per tile): the persistent kernel deals tiles out in a
+      // fixed stride, so this order balances the CTAs
+      const std::vector<MhtBlockDesc>& dd = desc[dir][s];
+      std::stable_sort(tcitems[dir][s].begin(), tcitems[dir][s].end(), [&](const MhtItem& a, const MhtItem& b) {
+        return (a.count > 0 ? dd[a.blk].cols : -1) > (b.count > 0 ? dd[b.blk].cols : -1);
+      });
       P.st[s].dir[dir].tc_nitems = int64_t(tcitems[dir][s].size());
     }
   }
@@ -263,6 +269,9 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
   pos = align_up(pos + size_t(F.n) * 4, 256);
   P.weights_off = pos;
   pos = align_up(pos + size_t(F.n) * sb, 256);
+  P.tmap_off = pos;
+  P.tmap_bytes = fp64 ? 0 : size_t(2) * nst * nb * 128;
+  pos = align_up(pos + P.tmap_bytes, 256);
   P.image.assign(pos, 0);
   uint8_t* img = P.image.data();
 

@@ -140,18 +140,19 @@ def test_batch_autotune_keeps_results(torch_cuda):
         assert _rel(after[i].cpu().numpy(), B.synthesize(F, Cs[i])) <= 1e-6
 
 
-def test_batch_tensor_core_form_matches_per_plan_apply(torch_cuda):
-    # 3xTF32 form: each instance's own apply (tensor cores from 16 real / 8 complex RHS) on
-    # forked streams inside one CUDA graph; equal bit for bit to the per-plan 3xTF32 apply
+@pytest.mark.parametrize("mode", ["6xbf16", "3xtf32"])
+def test_batch_tensor_core_form_matches_per_plan_apply(torch_cuda, mode):
+    # split tensor-core form: each instance's own apply (tensor cores from 16 real / 8 complex
+    # RHS) on forked streams inside one CUDA graph; equal bit for bit to the per-plan apply
     from paper_2605_21828_gb300 import Batch, Plan
     torch = torch_cuda
     inst = _inst()
     ks = [20, 9, 1, 17, 2, 16]  # wide tiles on the tensor cores, narrow ones on SIMT
     rng = np.random.default_rng(12)
     weights = [w if w is not None else rng.uniform(0.5, 1.5, F.n) for F, w, _ in inst]
-    plans = [Plan.from_factors(oracle_to_arrays(F), mode="3xtf32", weights=w)
+    plans = [Plan.from_factors(oracle_to_arrays(F), mode=mode, weights=w)
              for (F, _, _), w in zip(inst, weights)]
-    bt = Batch(plans, ks).bind().set_mode("3xtf32")
+    bt = Batch(plans, ks).bind().set_mode(mode)
     Cs = [W.gaussian_columns(F.m, k, 130 + i, complex_=F.complex_) for i, ((F, _, _), k) in enumerate(zip(inst, ks))]
     Gs = [W.gaussian_columns(F.n, k, 150 + i, complex_=F.complex_) for i, ((F, _, _), k) in enumerate(zip(inst, ks))]
     for i in range(len(inst)):

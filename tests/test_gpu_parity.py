@@ -19,7 +19,7 @@ from tests._bridge import oracle_to_arrays
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-6, "3xtf32": 1e-6}
+TOL = {"fp64": 1e-12, "fp32": 1e-6, "3xtf32": 1e-6, "6xbf16": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -244,7 +244,7 @@ def _fem_problem():
     return _FEM
 
 
-@pytest.mark.parametrize("mode", ["fp32", "3xtf32"])
+@pytest.mark.parametrize("mode", ["fp32", "3xtf32", "6xbf16"])
 @pytest.mark.parametrize("nrhs", [1, 64])
 def test_fem_deformed_sphere_matches_oracle_and_inverts(torch_cuda, mode, nrhs):
     from paper_2605_21828_gb300 import Plan
@@ -321,43 +321,49 @@ def test_repeated_applies_are_deterministic(torch_cuda):
     assert plan.check() == 0
 
 
+@pytest.mark.parametrize("mode", ["6xbf16", "3xtf32"])
 @pytest.mark.parametrize("nrhs", [16, 37, 64, 130])
-def test_tensor_core_3xtf32_matches_oracle(torch_cuda, nrhs):
-    # 3xTF32 tcgen05 block products (hi*hi + hi*lo + lo*hi, FP32 accumulation) for >= 16 RHS
+def test_tensor_core_split_products_match_oracle(torch_cuda, nrhs, mode):
+    # tcgen05 block products for >= 16 RHS with split operands: 6xBF16 (exact three-way split,
+    # six products) or 3xTF32 (hi*hi + hi*lo + lo*hi), FP32 accumulation
     from paper_2605_21828_gb300 import Plan
     torch = torch_cuda
     for n, lmax, leaf in ((1000, 31, 64), (4096, 63, 128)):
         F, _ = _sphere_factors(n, lmax, leaf, 1e-6)
         w = np.random.default_rng(2).uniform(0.5, 1.5, n)
-        plan = Plan.from_factors(oracle_to_arrays(F), mode="3xtf32", weights=w).bind(max_nrhs=nrhs)
+        plan = Plan.from_factors(oracle_to_arrays(F), mode=mode, weights=w).bind(max_nrhs=nrhs)
         C_ = W.gaussian_columns(F.m, nrhs, 31)
         f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
         assert plan.check() == 0
-        _check(f, B.synthesize(F, C_), "3xtf32")
+        _check(f, B.synthesize(F, C_), mode)
         G = W.gaussian_columns(n, nrhs, 41)
         a = plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy()
         assert plan.check() == 0
-        _check(a, B.analyze(F, G, w), "3xtf32")
+        _check(a, B.analyze(F, G, w), mode)
         fw = plan.synthesize_raw(_to_dev(torch, C_, plan), weighted=True).cpu().numpy()
-        _check(fw, w[:, None] * B.synthesize(F, C_), "3xtf32")
+        _check(fw, w[:, None] * B.synthesize(F, C_), mode)
+        s = np.random.default_rng(9).uniform(0.1, 2.0, F.m)  # diagonal fused into the leaf gather
+        fs = plan.synthesize_scaled(_to_dev(torch, C_, plan), torch.from_numpy(s).float().cuda()).cpu().numpy()
+        _check(fs, B.synthesize(F, s[:, None] * C_), mode)
 
 
+@pytest.mark.parametrize("mode", ["6xbf16", "3xtf32"])
 @pytest.mark.parametrize("nrhs", [8, 16, 21, 40])
-def test_tensor_core_3xtf32_complex_matches_oracle(torch_cuda, nrhs):
+def test_tensor_core_split_products_complex_match_oracle(torch_cuda, nrhs, mode):
     # complex factors on the tensor cores: one real product of twice the width per block
     from paper_2605_21828_gb300 import Plan
     torch = torch_cuda
     F, _ = _torus_factors(1024, 1024, 64, 1e-6)
     w = np.random.default_rng(3).uniform(0.5, 1.5, F.n)
-    plan = Plan.from_factors(oracle_to_arrays(F), mode="3xtf32", weights=w).bind(max_nrhs=nrhs)
+    plan = Plan.from_factors(oracle_to_arrays(F), mode=mode, weights=w).bind(max_nrhs=nrhs)
     C_ = W.gaussian_columns(F.m, nrhs, 51, complex_=True)
     f = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
     assert plan.check() == 0
-    _check(f, B.synthesize(F, C_), "3xtf32")
+    _check(f, B.synthesize(F, C_), mode)
     G = W.gaussian_columns(F.n, nrhs, 61, complex_=True)
     a = plan.analyze_raw(_to_dev(torch, G, plan), weighted=True).cpu().numpy()
     assert plan.check() == 0
-    _check(a, B.analyze(F, G, w), "3xtf32")
+    _check(a, B.analyze(F, G, w), mode)
     # the same plan in FP32 SIMT arithmetic agrees
     plan.set_mode("fp32")
     f32 = plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy()
@@ -371,12 +377,12 @@ def test_autotuned_configurations_keep_parity(torch_cuda):
     torch = torch_cuda
     F, _ = _sphere_factors(4096, 63, 128, 1e-6)
     w = np.random.default_rng(4).uniform(0.5, 1.5, F.n)
-    for mode, nrhs in (("fp32", 1), ("fp32", 5), ("3xtf32", 20), ("fp64", 3)):
+    for mode, nrhs in (("fp32", 1), ("fp32", 5), ("3xtf32", 20), ("6xbf16", 64), ("fp64", 3)):
         plan = Plan.from_factors(oracle_to_arrays(F), mode=mode, weights=w).bind(max_nrhs=nrhs)
         tuned = plan.autotune(nrhs)
         assert len(tuned) == 2 * (plan.levels + 2)
         assert all(t["ms"] > 0 for t in tuned)
-        if mode != "3xtf32":
+        if mode not in ("3xtf32", "6xbf16"):
             assert not any(t["tensor"] for t in tuned)
         C_ = W.gaussian_columns(F.m, nrhs, 71)
         _check(plan.synthesize_raw(_to_dev(torch, C_, plan)).cpu().numpy(), B.synthesize(F, C_), mode)
