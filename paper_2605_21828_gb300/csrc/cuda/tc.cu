@@ -76,6 +76,7 @@ struct TcParams {
   long long os_e, os_k;
   int nitems, ntiles, nrhs;
   int vec;                    // input rows of the RHS tile are contiguous and 16-byte aligned
+  int vec_out;                // output rows likewise (real plans)
   unsigned* status;
 };
 
@@ -290,6 +291,42 @@ __device__ __forceinline__ void put_pieces(unsigned char* base, int piece_bytes,
   }
 }
 
+// The same for 4 consecutive K values (K offset 4 k4 within the chunk).
+template <bool BF16>
+__device__ __forceinline__ void put_pieces4(unsigned char* base, int piece_bytes, int r, int k4, const float (&x)[4]) {
+  if constexpr (BF16) {
+    constexpr int SBO = kTcK * 2 / 16 * 128;  // 512
+    unsigned w[3][2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float a = x[2 * j], b = x[2 * j + 1];
+      const unsigned p0 = bf16x2(a, b);
+      a -= bf_lo(p0);
+      b -= bf_hi(p0);
+      const unsigned p1 = bf16x2(a, b);
+      a -= bf_lo(p1);
+      b -= bf_hi(p1);
+      w[0][j] = p0;
+      w[1][j] = p1;
+      w[2][j] = bf16x2(a, b);
+    }
+    const int off = (r >> 3) * SBO + (k4 >> 1) * 128 + (r & 7) * 16 + (k4 & 1) * 8;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) *reinterpret_cast<uint2*>(base + i * piece_bytes + off) = make_uint2(w[i][0], w[i][1]);
+  } else {
+    constexpr int SBO = kTcK * 4 / 16 * 128;  // 1024
+    float h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      h[j] = tf32_rna(x[j]);
+      l[j] = tf32_rna(x[j] - h[j]);
+    }
+    const int off = (r >> 3) * SBO + k4 * 128 + (r & 7) * 16;
+    *reinterpret_cast<float4*>(base + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(base + piece_bytes + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 struct Unit {
   MhtItem it;
   MhtBlockDesc d;
@@ -313,28 +350,36 @@ __device__ __forceinline__ Unit get_unit(const TcParams& p, int u) {
 
 // Shared memory of one CTA: raw A slots, two split stages, raw B slots, weights, barriers.
 template <int MODE, int N, bool C, bool BF16>
-__host__ __device__ constexpr size_t tc_smem(int ra, int rb) {
+__host__ __device__ constexpr size_t tc_smem(int ra, int rb, int ns) {
   constexpr int W = C ? 2 : 1;
   constexpr int NP = BF16 ? 3 : 2;
   constexpr int PE = BF16 ? 2 : 4;
   constexpr int STAGE = NP * (kTcM * kTcK * PE + N * kTcK * PE);
   constexpr int RAWB = (MODE == TC_ADJ_ID ? 2 : 1) * kTcK * (N / W) * W * 4;
-  return 1024 + size_t(ra) * kRawA + 2 * size_t(STAGE) + size_t(rb) * RAWB + size_t(rb) * kTcK * 4 + 8 * 8 * 4 +
-         8 * (4 + 2 * kTmemBufs) + 64;
+  return 1024 + size_t(ra) * kRawA + size_t(ns) * STAGE + size_t(rb) * RAWB + size_t(rb) * kTcK * 4 + 8 * 8 * 4 +
+         8 * (8 + 2 * kTmemBufs) + 64 + 2 * 32 * kMathWarps * 16;
 }
 constexpr size_t kTcMaxSmem = 227 * 1024;
-// Ring depths: as many raw A slots (TMA tiles in flight, up to 8) as fit beside four raw B
-// slots (fewer B slots, down to 2, before A drops below 3).
+// Ring depths: three split stages (so that splitting runs ahead of the MMAs) when four raw A
+// slots (TMA tiles in flight) and three raw B slots fit beside them, else two; then as many raw
+// A slots (up to 8) as fit beside four raw B slots (fewer B slots, down to 2, before A drops
+// below 3).
+template <int MODE, int N, bool C, bool BF16>
+__host__ __device__ constexpr int tc_ns() {
+  return tc_smem<MODE, N, C, BF16>(4, 3, 3) <= kTcMaxSmem ? 3 : 2;
+}
 template <int MODE, int N, bool C, bool BF16>
 __host__ __device__ constexpr int tc_ra() {
   int ra = 8;
-  while (tc_smem<MODE, N, C, BF16>(ra, 4) > kTcMaxSmem && ra > 3) --ra;
+  while (tc_smem<MODE, N, C, BF16>(ra, 4, tc_ns<MODE, N, C, BF16>()) > kTcMaxSmem && ra > 4) --ra;
+  while (tc_smem<MODE, N, C, BF16>(ra, 2, tc_ns<MODE, N, C, BF16>()) > kTcMaxSmem && ra > 2) --ra;
   return ra;
 }
 template <int MODE, int N, bool C, bool BF16>
 __host__ __device__ constexpr int tc_rb() {
   int rb = 4;
-  while (tc_smem<MODE, N, C, BF16>(tc_ra<MODE, N, C, BF16>(), rb) > kTcMaxSmem && rb > 2) --rb;
+  while (tc_smem<MODE, N, C, BF16>(tc_ra<MODE, N, C, BF16>(), rb, tc_ns<MODE, N, C, BF16>()) > kTcMaxSmem && rb > 2)
+    --rb;
   return rb;
 }
 
@@ -360,23 +405,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte aligned base (the 128-byte swizzle pattern repeats every 1024 bytes)
   unsigned char* sm = smem_raw + ((1024 - (sa(smem_raw) & 1023)) & 1023);
-  constexpr int RA = tc_ra<MODE, N, C, BF16>(), RB = tc_rb<MODE, N, C, BF16>();
-  static_assert(tc_smem<MODE, N, C, BF16>(RA, RB) <= kTcMaxSmem, "shared memory of the tensor-core kernel");
+  constexpr int RA = tc_ra<MODE, N, C, BF16>(), RB = tc_rb<MODE, N, C, BF16>(), NS = tc_ns<MODE, N, C, BF16>();
+  static_assert(tc_smem<MODE, N, C, BF16>(RA, RB, NS) <= kTcMaxSmem, "shared memory of the tensor-core kernel");
   unsigned char* rawA = sm;                                  // [RA][16 KB], 1024-aligned
-  unsigned char* stages = rawA + size_t(RA) * kRawA;         // [2][STAGE], 1024-aligned
-  unsigned char* rawB = stages + 2 * STAGE;                  // [RB][RAWB]
+  unsigned char* stages = rawA + size_t(RA) * kRawA;         // [NS][STAGE], 1024-aligned
+  unsigned char* rawB = stages + NS * STAGE;                 // [RB][RAWB]
   float* kw = reinterpret_cast<float*>(rawB + size_t(RB) * RAWB);  // [RB][32]
   uint64_t* bars = reinterpret_cast<uint64_t*>(kw + RB * kTcK);
   uint64_t* a_full = bars;           // [RA]
   uint64_t* a_empty = a_full + 8;    // [RA]
   uint64_t* b_full = a_empty + 8;    // [RB]
   uint64_t* b_empty = b_full + 8;    // [RB]
-  uint64_t* s_full = b_empty + 8;    // [2] split stage written
-  uint64_t* mma_done = s_full + 2;   // [2] chunk's MMAs complete (split stage free)
-  uint64_t* t_full = mma_done + 2;   // [kTmemBufs] chunk's sums ready in TMEM buffer
+  uint64_t* s_full = b_empty + 8;    // [NS] split stage written
+  uint64_t* mma_done = s_full + 4;   // [NS] chunk's MMAs complete (split stage free)
+  uint64_t* t_full = mma_done + 4;   // [kTmemBufs] chunk's sums ready in TMEM buffer
   uint64_t* t_empty = t_full + kTmemBufs;  // [kTmemBufs] TMEM buffer drained
   unsigned* tmem_slot = reinterpret_cast<unsigned*>(t_empty + kTmemBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // per split/drain thread, two unit slots: output offset, identity-term offset, weight of its row
+  int4* epi = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(bars) + 8 * (8 * 4 + 8 + 2 * kTmemBufs) + 64);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nunits = p.nitems * p.ntiles;
@@ -389,7 +436,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       mbar_init(&b_full[i], 32);  // one gather warp's cp.async arrivals per chunk
       mbar_init(&b_empty[i], kMathWarps);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(&s_full[i], kMathWarps);
       mbar_init(&mma_done[i], 1);
     }
@@ -444,9 +491,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         const Unit x = get_unit<N, C>(p, u);
         for (int c = 0; c < x.nch; ++c, ++g) {
-          const int s = g & 1, b = g % kTmemBufs;
+          const int s = g % NS, b = g % kTmemBufs;
           if (!waitb(&t_empty[b], unsigned((g / kTmemBufs) & 1) ^ 1u, abort_flag, p.status) ||
-              !waitb(&s_full[s], unsigned((g >> 1) & 1), abort_flag, p.status)) {
+              !waitb(&s_full[s], unsigned((g / NS) & 1), abort_flag, p.status)) {
             ok = false;
             break;
           }
@@ -565,65 +612,111 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
     static_assert(kMathWarps % 4 == 0, "whole groups of four warps cover the 128 TMEM lanes");
     const int row = quad * 32 + lane;  // TMEM lane = tile row of this thread
     const bool in_w = p.wts && (MODE == TC_SYN_ID || MODE == TC_ADJ_U);
-    float acc[H], cmp[H];
+    // Kahan sums of this thread's H columns, in pairs for the packed FP32 instructions: value =
+    // acc + cmn (cmn holds the negated compensation)
+    float2 acc[H / 2], cmn[H / 2];
 #pragma unroll
-    for (int j = 0; j < H; ++j) acc[j] = cmp[j] = 0.f;
+    for (int j = 0; j < H / 2; ++j) acc[j] = cmn[j] = make_float2(0.f, 0.f);
     // chunks converted but not yet drained (at most two): unit index << 1 | last chunk of its unit
     int pq0 = 0, pq1 = 0, np = 0;
     bool ok = true;
     int g = 0, gdr = 0;  // chunks converted, chunks drained
 
-    // waits (lane 0) with the verdict shared by the warp
+    // every lane polls the barrier itself; a lane that gave up sets the abort flag, which makes
+    // the others give up as well, so the warp leaves together (the verdict is taken by vote)
     auto wwait = [&](uint64_t* b, unsigned ph) -> bool {
-      int r = 1;
-      if (lane == 0) r = waitb(b, ph, abort_flag, p.status) ? 1 : 0;
-      return __shfl_sync(0xffffffffu, r, 0) != 0;
+      const bool r = waitb(b, ph, abort_flag, p.status);
+      return __all_sync(0xffffffffu, r);
     };
-    // rows of a unit: acc (Kahan-compensated sums) + identity term / weights, to the output
-    auto epilogue = [&](const Unit& x) {
+    // Per-unit epilogue data of this thread's row, prepared when the unit starts: the index loads
+    // are issued before the unit's first split and their results stored afterwards, so that
+    // their latency hides behind the split; the epilogue itself then only loads the identity
+    // terms and stores.  A pending entry packs the unit's scalars: last chunk (bit 0), record
+    // slot (1), sibling buffer (2), rows (3..10), right-hand sides in the tile (11..17).
+    const int col0 = quarter * H;
+    const int cc0 = C ? col0 / NR : 0;  // complex: real parts, then imaginary parts
+    const int n0 = C ? col0 % NR : col0;
+    int us = 0;  // units started by this CTA (record slot = us & 1)
+    auto epi_issue = [&](const Unit& x, int& ld0) {  // index load of the row (-1 if none)
+      ld0 = -1;
       if (row < x.it.count) {
         const int i = x.it.start + row;
-        long long dst;
-        float wrow = 1.f;
-        long long sidx = -1;
-        float wsk = 1.f;
+        if (MODE == TC_SYN_ID) ld0 = p.idx[x.d.idx_off + i];
+        else if (MODE == TC_ADJ_ID) ld0 = p.idx[x.d.idx_off + x.d.cols + i];
+        else if (MODE == TC_SYN_U) ld0 = p.perm[x.d.out_off + i];
+      }
+    };
+    auto epi_store = [&](const Unit& x, int ld0, int slot) -> int {
+      int4 e = make_int4(0, 0, 0, __float_as_int(1.f));
+      if (row < x.it.count) {
+        const int i = x.it.start + row;
+        long long dst = 0;
+        float w = 1.f;
         if (MODE == TC_SYN_ID) {
           dst = (long long)x.d.out_off + i;
-          sidx = p.idx[x.d.idx_off + i];
-          if (p.wts) wsk = p.wts[sidx];
+          if (p.wts) w = p.wts[ld0];  // the leaf stage's scale of the skeleton coefficient
+          e.z = int(((long long)ld0 * p.is_e + (long long)(x.r0 + n0) * p.is_k) * W + cc0);
         } else if (MODE == TC_ADJ_ID) {
-          dst = p.idx[x.d.idx_off + x.d.cols + i];
+          dst = ld0;
         } else if (MODE == TC_SYN_U) {
-          dst = p.perm[x.d.out_off + i];
-          if (p.wts) wrow = p.wts[dst];
+          dst = ld0;
+          if (p.wts) w = p.wts[ld0];
         } else {
           dst = (long long)x.d.in_off + i;
         }
-        // this thread's H columns are consecutive right-hand sides of one component
-        const int col0 = quarter * H;
-        const int cc = C ? col0 / NR : 0;  // complex: real parts, then imaginary parts
-        const int n0 = C ? col0 % NR : col0;
-        float* o = ((MODE == TC_ADJ_ID && x.it.sib) ? p.out1 : p.out0) +
-                   (dst * p.os_e + (long long)(x.r0 + n0) * p.os_k) * W + cc;
-        const long long ostep = p.os_k * W;
-        const float* ip = p.in0;  // identity term of the synthesis ID stage
-        if (MODE == TC_SYN_ID) ip += (sidx * p.is_e + (long long)(x.r0 + n0) * p.is_k) * W + cc;
-        const long long istep = p.is_k * W;
-        const int nv = min(H, x.nk - n0);
+        const long long o = (dst * p.os_e + (long long)(x.r0 + n0) * p.os_k) * W + cc0;
+        e.x = int(o & 0xffffffff);
+        e.y = int(o >> 32);
+        e.w = __float_as_int(w);
+      }
+      epi[slot * 32 * kMathWarps + mt] = e;
+      return (slot << 1) | ((MODE == TC_ADJ_ID && x.it.sib) ? 4 : 0) | (x.it.count << 3) | (x.nk << 11);
+    };
+    // rows of a unit: acc (Kahan-compensated sums) + identity term / weights, to the output
+    auto epilogue = [&](int entry) {
+      const int count = (entry >> 3) & 255, nk = (entry >> 11) & 127;
+      if (row < count) {
+        const int4 e = epi[((entry >> 1) & 1) * 32 * kMathWarps + mt];
+        const long long ooff = (long long)(unsigned)e.x | ((long long)e.y << 32);
+        float* o = ((entry & 4) ? p.out1 : p.out0) + ooff;
+        const float* ip = p.in0 + e.z;  // identity term of the synthesis ID stage
+        const float w = __int_as_float(e.w);
+        const int nv = min(H, nk - n0);
+        float v[H];
 #pragma unroll
-        for (int j = 0; j < H; ++j) {
-          if (j < nv) {
-            float v = acc[j] - cmp[j];
-            if (MODE == TC_SYN_ID) v += wsk * *ip;
-            if (MODE == TC_SYN_U) v *= wrow;
-            *o = v;
+        for (int j = 0; j < H; ++j) v[j] = (j & 1) ? acc[j >> 1].y + cmn[j >> 1].y : acc[j >> 1].x + cmn[j >> 1].x;
+        if (MODE == TC_SYN_ID) {
+          if (!C && p.vec && nv == H) {  // contiguous real rows: 16-byte loads
+#pragma unroll
+            for (int j = 0; j < H; j += 4) {
+              const float4 t = *reinterpret_cast<const float4*>(ip + j);
+              v[j] += w * t.x;
+              v[j + 1] += w * t.y;
+              v[j + 2] += w * t.z;
+              v[j + 3] += w * t.w;
+            }
+          } else {
+            const long long istep = p.is_k * W;
+#pragma unroll
+            for (int j = 0; j < H; ++j)
+              if (j < nv) v[j] += w * ip[j * istep];
           }
-          o += ostep;
-          ip += istep;
+        }
+        if (MODE == TC_SYN_U)
+#pragma unroll
+          for (int j = 0; j < H; ++j) v[j] *= w;
+        if (p.vec_out && nv == H) {
+#pragma unroll
+          for (int j = 0; j < H; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+          const long long ostep = p.os_k * W;
+#pragma unroll
+          for (int j = 0; j < H; ++j)
+            if (j < nv) o[j * ostep] = v[j];
         }
       }
 #pragma unroll
-      for (int j = 0; j < H; ++j) acc[j] = cmp[j] = 0.f;
+      for (int j = 0; j < H / 2; ++j) acc[j] = cmn[j] = make_float2(0.f, 0.f);
     };
     // drain of chunk gdr, first half: wait for its sums and start reading this thread's H
     // columns of its TMEM buffer (the read completes in drain_finish)
@@ -642,14 +735,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&t_empty[gdr % kTmemBufs]);
       ++gdr;
+      const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-      for (int n = 0; n < H; ++n) {
-        const float y = d[n] - cmp[n];
-        const float tt = acc[n] + y;
-        cmp[n] = (tt - acc[n]) - y;
+      for (int n = 0; n < H / 2; ++n) {  // Kahan: y = d - c, t = acc + y, c = (t - acc) - y
+        const float2 y = __fadd2_rn(make_float2(d[2 * n], d[2 * n + 1]), cmn[n]);
+        const float2 tt = __fadd2_rn(acc[n], y);
+        cmn[n] = __fadd2_rn(__ffma2_rn(tt, m1, acc[n]), y);  // (acc - t) + y, exact a - t by the FMA
         acc[n] = tt;
       }
-      if (entry & 1) epilogue(get_unit<N, C>(p, entry >> 1));
+      if (entry & 1) epilogue(entry);
     };
     auto drain_one = [&](int entry) -> bool {
       float d[H];
@@ -657,13 +751,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       drain_finish(d, entry);
       return true;
     };
-    // splits chunk c of unit x (global index gg) into stage gg & 1
-    auto convert = [&](const Unit& x, int c, int gg) -> bool {
+    // waits for chunk gg's raw tiles (and, with two stages, for the stage to be free)
+    auto convert_wait = [&](int gg) -> bool {
+      // the stage's previous chunk (gg - NS) must have been consumed by its MMAs.  With three
+      // stages this is already known: the drain two chunks behind the split has seen the sums
+      // of every chunk up to gg - 3 complete
+      if (NS < 3 && !wwait(&mma_done[gg % NS], unsigned((gg / NS) & 1) ^ 1u)) return false;
+      return wwait(&a_full[gg % RA], unsigned((gg / RA) & 1)) && wwait(&b_full[gg % RB], unsigned((gg / RB) & 1));
+    };
+    // splits chunk gg (its raw tiles have arrived) into stage gg % NS
+    auto convert = [&](int gg) {
       const int sa_ = gg % RA, sb_ = gg % RB;
-      // the stage's previous chunk (gg - 2) must have been consumed by its MMAs
-      if (!wwait(&mma_done[gg & 1], unsigned((gg >> 1) & 1) ^ 1u)) return false;
-      if (!wwait(&a_full[sa_], unsigned((gg / RA) & 1)) || !wwait(&b_full[sb_], unsigned((gg / RB) & 1))) return false;
-      unsigned char* st = stages + (gg & 1) * STAGE;
+      unsigned char* st = stages + (gg % NS) * STAGE;
       // A: raw 128 x 32 FP32 tile, 128-byte rows, 16-byte chunk j of row r at position j ^ (r & 7)
       const unsigned char* ra = rawA + size_t(sa_) * kRawA;
 #pragma unroll
@@ -674,16 +773,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
         const float xv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
         put_pieces<BF16>(st, A_PIECE, r, k8, xv);
       }
-      // B': row n (accumulator column), K = 32 real columns
+      // B: row n (accumulator column) x 4 of the 32 real K columns per thread
       const float* rb = reinterpret_cast<const float*>(rawB + size_t(sb_) * RAWB);
       const float* kws = kw + sb_ * kTcK;
-      for (int e = mt; e < 4 * N; e += 32 * kMathWarps) {
-        const int n = e % N, k8 = e / N;
-        float xv[8];
+      for (int e = mt; e < 8 * N; e += 32 * kMathWarps) {
+        const int n = e % N, k4 = e / N;
+        float xv[4];
         if (!C) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int k = k8 * 8 + j;
+          for (int j = 0; j < 4; ++j) {
+            const int k = k4 * 4 + j;
             float v = rb[k * NR + n];
             if (NB == 2) v += rb[KW * NR + k * NR + n];
             if (in_w) v *= kws[k];
@@ -692,8 +791,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
         } else {
           const int rn = n < NR ? n : n - NR;  // right-hand side of this column
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int k = k8 * 4 + j;  // complex entry
+          for (int j = 0; j < 2; ++j) {
+            const int k = k4 * 2 + j;  // complex entry
             float2 v = *reinterpret_cast<const float2*>(rb + (k * NR + rn) * 2);
             if (NB == 2) {
               const float2 v1 = *reinterpret_cast<const float2*>(rb + (KW * NR + k * NR + rn) * 2);
@@ -710,16 +809,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
           }
         }
         // piece j of B (N rows) sits at + j * B_PIECE
-        put_pieces<BF16>(st + NP * A_PIECE, B_PIECE, n, k8, xv);
+        put_pieces4<BF16>(st + NP * A_PIECE, B_PIECE, n, k4, xv);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&s_full[gg & 1]);
+        mbar_arrive(&s_full[gg % NS]);
         mbar_arrive(&a_empty[sa_]);
         mbar_arrive(&b_empty[sb_]);
       }
-      return true;
     };
 
     for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
@@ -745,22 +843,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
           --np;
         }
         if (!ok) break;
-        epilogue(x);
+        int ld0;
+        epi_issue(x, ld0);
+        epilogue(epi_store(x, ld0, us++ & 1) | 1);
         continue;
       }
+      int ld0 = -1, ue = 0;  // the unit's epilogue record: index load, then packed entry
+      epi_issue(x, ld0);
       for (int c = 0; c < x.nch; ++c, ++g) {
-        // the chunk two back drains after this chunk's split; the previous chunk's MMAs run
-        // meanwhile
-        const bool dr = np == 2;
-        if (!(ok = convert(x, c, g))) break;
-        if (dr) {
+        // the chunk two back drains before this chunk's split: its TMEM read is in flight while
+        // this chunk's tiles are waited for; the previous chunk's MMAs run meanwhile
+        if (np == 2) {
           float d[H];
           if (!(ok = drain_start(d))) break;
+          if (!(ok = convert_wait(g))) break;
           drain_finish(d, pq0);
           pq0 = pq1;
           np = 1;
+        } else if (!(ok = convert_wait(g))) {
+          break;
         }
-        const int e = (u << 1) | (c == x.nch - 1 ? 1 : 0);
+        convert(g);
+        if (c == 0) ue = epi_store(x, ld0, us++ & 1);  // after the drains of the previous unit
+        const int e = ue | (c == x.nch - 1 ? 1 : 0);
         if (np == 0) pq0 = e;
         else pq1 = e;
         ++np;
@@ -781,7 +886,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       for (long long j = (a_issued > RA ? a_issued - RA : 0ll); j < a_issued; ++j)
         wait_quiet(&a_full[j % RA], unsigned((j / RA) & 1));
     if (warp == 1 && lane == 0 && mma_issued > 0)
-      wait_quiet(&mma_done[(mma_issued - 1) & 1], unsigned(((mma_issued - 1) >> 1) & 1));
+      wait_quiet(&mma_done[(mma_issued - 1) % NS], unsigned(((mma_issued - 1) / NS) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -795,7 +900,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
 template <int MODE, int N, bool C, bool BF16>
 int launch_n(const TcLaunch& a, std::string& err) {
   constexpr int NR = C ? N / 2 : N;
-  size_t smem = tc_smem<MODE, N, C, BF16>(tc_ra<MODE, N, C, BF16>(), tc_rb<MODE, N, C, BF16>());
+  size_t smem =
+      tc_smem<MODE, N, C, BF16>(tc_ra<MODE, N, C, BF16>(), tc_rb<MODE, N, C, BF16>(), tc_ns<MODE, N, C, BF16>());
   // one CTA per SM: its tensor-memory allocation is sized for the whole SM's share
   smem = std::max<size_t>(smem, 120 * 1024);
   auto kern = k_tcs<MODE, N, C, BF16>;
@@ -827,6 +933,8 @@ int launch_n(const TcLaunch& a, std::string& err) {
   const auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
   p.vec = (a.is_k == 1 && (a.is_e * W) % 4 == 0 && (a.nrhs * W) % 4 == 0 && al16(a.in0) && (!a.in1 || al16(a.in1)))
               ? 1 : 0;
+  p.vec_out = (!C && a.os_k == 1 && a.os_e % 4 == 0 && (a.nrhs % 4) == 0 && al16(a.out0) && (!a.out1 || al16(a.out1)))
+                  ? 1 : 0;
   p.status = a.status;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
