@@ -812,12 +812,6 @@ int tc_launch(const Ctx& c, int s, int dir, int mode, const void* in0, const voi
   a.mode = mode;
   a.cplx = c.P.cplx ? 1 : 0;
   a.bf16 = c.mode == MHT_APPLY_6XBF16 ? 1 : 0;
-  static const int drain_chunks = [] {
-    const char* e = std::getenv("MHT_TC_DRAIN_CHUNKS");
-    return e && std::atoi(e) == 1 ? 1 : 2;
-  }();
-  // the two-way TF32 split already spends most of the FP32 error budget: drain every chunk
-  a.drain_chunks = a.bf16 ? drain_chunks : 1;
   a.tmaps = c.d.base + c.P.tmap_off + size_t(dir * (c.P.L + 2) + s) * c.P.nb * 128;
   a.status = status_ptr(c);
   a.stream = c.s;

@@ -6,8 +6,9 @@
 // transposes for the adjoint), N = k, K = its columns.  The tensor cores multiply low-precision
 // operands exactly and accumulate in FP32, so every FP32 operand is split into pieces and the
 // significant piece products are summed:
-//   * 6xBF16 (MHT_APPLY_6XBF16): x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0),
-//     x2 = x - x0 - x1 (exact: three 8-bit significands cover FP32's 24 bits), and
+//   * 6xBF16 (MHT_APPLY_6XBF16): x = x0 + x1 + x2 with x0 the leading 8 significant bits of x,
+//     x1 those of x - x0 (Veltkamp-Dekker splitting) and x2 = x - x0 - x1 (exact: three 8-bit
+//     significands cover FP32's 24 bits), and
 //     a b ~ a0 b0 + (a0 b1 + a1 b0) + (a0 b2 + a1 b1 + a2 b0); the dropped terms are below
 //     2^-23 |a b|.
 //   * 3xTF32 (MHT_APPLY_3XTF32): x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (22 of 24
@@ -218,30 +219,34 @@ __device__ __forceinline__ void tmem_wait(float (&v)[K]) {
 }
 
 // ---------------------------------------------------------------- operand splitting
-// Two FP32 values -> BF16 pieces, packed (element 0 in the low half, as it sits in memory).
-__device__ __forceinline__ unsigned bf16x2(float lo, float hi) {
-  unsigned d;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
+// Veltkamp-Dekker splitting of two values at once (packed FP32): c = x (2^16 + 1),
+// hi = c - (c - x) keeps the leading 8 significant bits of x (exactly representable in BF16),
+// lo = x - hi is exact.  Full-rate FMA-pipe arithmetic instead of conversion instructions.
+__device__ __forceinline__ void vsplit2(float2 x, float2& hi, float2& lo) {
+  const float2 k = make_float2(65537.f, 65537.f), m1 = make_float2(-1.f, -1.f);
+  const float2 c = __fmul2_rn(x, k);
+  const float2 t = __ffma2_rn(x, m1, c);  // c - x
+  hi = __ffma2_rn(t, m1, c);              // c - t
+  lo = __ffma2_rn(hi, m1, x);             // x - hi, exact
 }
-__device__ __forceinline__ float bf_lo(unsigned d) { return __uint_as_float(d << 16); }
-__device__ __forceinline__ float bf_hi(unsigned d) { return __uint_as_float(d & 0xffff0000u); }
+// upper halves (the BF16 bits) of two FP32 values that are exactly BF16: element a in the low half
+__device__ __forceinline__ unsigned pack_hi(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+// x = x0 + x1 + x2 exactly for 2 values: three packed BF16 words
+__device__ __forceinline__ void split3_pair(float a, float b, unsigned& w0, unsigned& w1, unsigned& w2) {
+  float2 h0, r0, h1, r1;
+  vsplit2(make_float2(a, b), h0, r0);
+  vsplit2(r0, h1, r1);  // r1 has at most 8 significant bits: exactly BF16
+  w0 = pack_hi(h0.x, h0.y);
+  w1 = pack_hi(h1.x, h1.y);
+  w2 = pack_hi(r1.x, r1.y);
+}
 // x = x0 + x1 + x2 exactly for 8 values; p[i] = piece i as four packed words
 __device__ __forceinline__ void split_bf16(const float (&x)[8], uint4 (&p)[3]) {
   unsigned w[3][4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    float a = x[2 * j], b = x[2 * j + 1];
-    const unsigned p0 = bf16x2(a, b);
-    a -= bf_lo(p0);
-    b -= bf_hi(p0);
-    const unsigned p1 = bf16x2(a, b);
-    a -= bf_lo(p1);
-    b -= bf_hi(p1);
-    w[0][j] = p0;
-    w[1][j] = p1;
-    w[2][j] = bf16x2(a, b);
-  }
+  for (int j = 0; j < 4; ++j) split3_pair(x[2 * j], x[2 * j + 1], w[0][j], w[1][j], w[2][j]);
 #pragma unroll
   for (int i = 0; i < 3; ++i) p[i] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
 }
@@ -298,18 +303,7 @@ __device__ __forceinline__ void put_pieces4(unsigned char* base, int piece_bytes
     constexpr int SBO = kTcK * 2 / 16 * 128;  // 512
     unsigned w[3][2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      float a = x[2 * j], b = x[2 * j + 1];
-      const unsigned p0 = bf16x2(a, b);
-      a -= bf_lo(p0);
-      b -= bf_hi(p0);
-      const unsigned p1 = bf16x2(a, b);
-      a -= bf_lo(p1);
-      b -= bf_hi(p1);
-      w[0][j] = p0;
-      w[1][j] = p1;
-      w[2][j] = bf16x2(a, b);
-    }
+    for (int j = 0; j < 2; ++j) split3_pair(x[2 * j], x[2 * j + 1], w[0][j], w[1][j], w[2][j]);
     const int off = (r >> 3) * SBO + (k4 >> 1) * 128 + (r & 7) * 16 + (k4 & 1) * 8;
 #pragma unroll
     for (int i = 0; i < 3; ++i) *reinterpret_cast<uint2*>(base + i * piece_bytes + off) = make_uint2(w[i][0], w[i][1]);

@@ -219,7 +219,6 @@ struct TcLaunch {
   int mode;  // 0 synthesis ID stage, 1 adjoint ID stage, 2 synthesis column bases, 3 adjoint
   int cplx;  // complex factors and vectors (interleaved float pairs)
   int bf16;  // 1: 6xBF16 split products, 0: 3xTF32
-  int drain_chunks = 2;  // chunks of 32 columns a tensor-memory accumulation spans (1 or 2)
   const void* tmaps;  // the stage's tensor maps (one per block, this direction) in the image
   unsigned* status;
   void* stream;
