@@ -5,13 +5,18 @@ The oracle cannot hold this Phi (34 GB in FP64), so it checks what it can comput
 and properties that hold at any size:
   * sampled rows of f = Phi c against the exact rows of Phi (normalized Legendre recurrence):
     the butterfly error is about eps (Sec. 6), so within 20 eps in relative l2 over the sample;
-  * the adjoint identity <Phi c, W g> = <c, Phi^T W g> for the library's own apply pair.
+  * the adjoint identity <Phi c, W g> = <c, Phi^T W g> for the library's own apply pair;
+and, element by element, the kernels against the oracle's FP64 apply (Sec. 2, stage by stage)
+of the same plan's exported factors (15 GB of FP64 on the host): relative l2 <= 1e-6, the
+FP32 kernel tolerance, for synthesis and weighted analysis.
 """
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import butterfly as B
 from oracle import harmonics as H
+from tests._bridge import arrays_to_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -37,3 +42,8 @@ def test_full_size_sphere_sampled_rows_and_adjoint_identity(mht_lib):
     lhs = float(np.dot(f, w * g))
     rhs = float(np.dot(c, a))
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(f) * np.linalg.norm(w * g)
+    # the kernels' rounding against the oracle's FP64 apply of the same factors
+    F = arrays_to_oracle(plan.export())
+    for got, ref in ((f, B.synthesize(F, c)), (a, B.analyze(F, g, w))):
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
