@@ -8,8 +8,12 @@ c = Phi^T W f of `--nrhs` vectors; value = vectors transformed (both directions)
 over all ranks.  Inputs are resident in HBM; the packed factors (GBs) are far larger than
 L2, so every step streams them from HBM (no flush needed).
 
-`--impl reference` times the FP64 CPU oracle (direct summation with matrix-free rows of
-Phi) on a bounded sample of rows per step, scaled to whole transforms.
+`--impl reference` times the FP64 CPU oracle on the same workload: its butterfly apply (Sec. 2,
+stage by stage, numpy/BLAS on the host cores) of the plan's exported factors, one whole
+transform pair per step.
+
+`--gpus N` (N > 1) without a launcher starts N replicas itself (torch.distributed.run on this
+node, one rank per GPU); under a launcher (WORLD_SIZE set) every rank runs one replica.
 """
 from __future__ import annotations
 
@@ -52,11 +56,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--multi-rhs", type=int, default=64, help="extra measurement at this many RHS (0: off)")
-    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64", "torus_sweep", "peaks"],
+    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64", "torus_sweep", "peaks", "ranks"],
                     help="batch64: 64 ragged instances (torus / sphere / deformed sphere, n in [2000, 40000], "
                          "m = n/4, 1-128 RHS each) in one persistent launch per direction; torus_sweep: the flat-torus "
                          "memory law (m = ceil(n/25), eps 1e-3 and 1e-6) with single-RHS apply times; peaks: "
-                         "the GEMM rates the multi-RHS rooflines divide by (TF32, FP32, FP64, BF16)")
+                         "the GEMM rates the multi-RHS rooflines divide by (TF32, FP32, FP64, BF16); ranks: "
+                         "the rank layout of a replica launch (gloo, no GPU work)")
     ap.add_argument("--plan-cache", default=os.environ.get("MHT_PLAN_CACHE", ""))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -77,49 +82,113 @@ def workload_desc(name):
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
-def oracle_sample_step(X, c, w, rows, lmax):
-    """Oracle direct summation restricted to `rows`: f(rows) = Phi(rows,:) c and the
-    contribution Phi(rows,:)^T (w f)(rows) to the adjoint.  Returns (wall, process CPU) seconds."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def blas_threads(k):
+    """Sets the thread count of numpy's bundled OpenBLAS (when its control symbol is found);
+    returns the previous count, or None when it cannot be set."""
+    import ctypes
+    import glob
+
     import numpy as np
+    libdir = os.path.join(os.path.dirname(np.__file__), "..", "numpy.libs")
+    for lib in glob.glob(os.path.join(libdir, "*openblas*")):
+        try:
+            h = ctypes.CDLL(lib)
+        except OSError:
+            continue
+        for prefix in ("scipy_openblas", "openblas"):
+            for suffix in ("64_", ""):
+                get = getattr(h, f"{prefix}_get_num_threads{suffix}", None)
+                put = getattr(h, f"{prefix}_set_num_threads{suffix}", None)
+                if get is not None and put is not None:
+                    prev = int(get())
+                    put(ctypes.c_int(int(k)))
+                    return prev
+    return None
 
-    from oracle import harmonics as H
+
+def oracle_factors(plan):
+    """The plan's FP64 factors in the oracle's form (array reshaping only)."""
+    from tests._bridge import arrays_to_oracle
+    return arrays_to_oracle(plan.export())
+
+
+def oracle_step(F, c, w):
+    """One step of the reference: the oracle's FP64 butterfly apply (Sec. 2, stage by stage) of
+    synthesis f = Phi c and weighted analysis Phi^T W f.  Returns (wall, process CPU) seconds."""
+    from oracle import butterfly as B
     t0, p0 = time.perf_counter(), time.process_time()
-    Phi = H.sphere_phi(X[rows], lmax)
-    f = Phi @ c
-    _ = Phi.T @ (w[rows] * f)
-    dt, cpu = time.perf_counter() - t0, time.process_time() - p0
-    del Phi
-    np.asarray(f)
-    return dt, cpu
+    f = B.synthesize(F, c)
+    B.analyze(F, f, w)
+    return time.perf_counter() - t0, time.process_time() - p0
 
 
-def cpu_baseline(name, budget_s=15.0, steps=None):
+def cpu_baseline(F, c, w, steps, warmup=1):
+    """The oracle's butterfly apply of the same plan on the host: whole transforms, numpy/BLAS
+    on every core the process may use; plus one transform with BLAS limited to a single thread."""
+    for _ in range(max(1, warmup)):
+        oracle_step(F, c, w)
+    runs = [oracle_step(F, c, w) for _ in range(max(1, steps))]
+    wall = sum(r[0] for r in runs)
+    used = sum(r[1] for r in runs) / max(wall, 1e-9)
+    single = None
+    prev = blas_threads(1)
+    if prev is not None:
+        single = 1.0 / oracle_step(F, c, w)[0]
+        blas_threads(prev)
+    avail = len(os.sched_getaffinity(0))
+    meta = {"kind": "oracle", "cores": max(1, round(used)), "cpu_time_per_wall_time": round(used, 2),
+            "cores_available": avail, "cpu_model": cpu_model(), "single_core_transforms_per_s": single,
+            "sample": f"{len(runs)} whole transforms (synthesis + weighted analysis of one vector): the oracle's "
+                      f"FP64 butterfly apply of the plan's exported factors, numpy with BLAS on up to {avail} "
+                      f"threads"}
+    return len(runs) / wall, meta, [r[0] for r in runs]
+
+
+def direct_summation_sample(name, budget_s=15.0):
+    """The exact transform by direct summation (rows of Phi by the normalized Legendre
+    recurrence) on a random sample of rows, scaled to whole transforms by n / rows."""
     import numpy as np
 
     import workloads as W
+    from oracle import harmonics as H
     n, lmax, leaf, eps = WORKLOADS[name]
     X = W.fibonacci_points(n)
     m = (lmax + 1) ** 2
     c = W.sphere_coefficients(m)[:, 0]
     w = np.full(n, 4 * np.pi / n)
     rng = np.random.default_rng(0)
+
+    def rows_step(rows):
+        t0 = time.perf_counter()
+        Phi = H.sphere_phi(X[rows], lmax)
+        f = Phi @ c
+        _ = Phi.T @ (w[rows] * f)
+        return time.perf_counter() - t0
+
     rows = np.sort(rng.choice(n, 256, replace=False))
-    t, _ = oracle_sample_step(X, c, w, rows, lmax)
-    per_row = t / len(rows)
-    s = int(min(n, max(256, budget_s / max(per_row, 1e-9) / (steps or 1))))
+    per_row = rows_step(rows) / len(rows)
+    s = int(min(n, max(256, budget_s / max(per_row, 1e-9))))
     rows = np.sort(rng.choice(n, s, replace=False))
-    runs = [oracle_sample_step(X, c, w, rows, lmax) for _ in range(steps or 1)]
-    times = [r[0] for r in runs]
-    t_full = statistics.median(times) * n / s
-    avail = len(os.sched_getaffinity(0))
-    # threads actually used: process CPU time over wall time (the numpy recurrence runs on
-    # one thread, the BLAS products on several)
-    used = sum(r[1] for r in runs) / max(sum(times), 1e-9)
-    return 1.0 / t_full, {"kind": "oracle", "cores": max(1, round(used)), "cpu_time_per_wall_time": round(used, 2),
-                          "cores_available": avail,
-                          "sample": f"{s} of {n} rows per step (Phi rows by the normalized Legendre recurrence, "
-                                    f"f = Phi c and Phi^T W f restricted to them), scaled by n/{s}; numpy "
-                                    f"(one thread) and BLAS (up to {avail} threads)"}, times
+    t = rows_step(rows)
+    return {"value": 1.0 / (t * n / s), "unit": "transforms/s", "sample": f"{s} of {n} rows, scaled by n/{s}"}
 
 
 def run_reference(args):
@@ -128,14 +197,23 @@ def run_reference(args):
         return
     if args.workload not in WORKLOADS:
         raise SystemExit("--impl reference times the oracle on the single-plan workloads only")
+    import numpy as np
+
+    import workloads as W
+    from paper_2605_21828_gb300.build import build_library
+    build_library()
     desc = workload_desc(args.workload)
+    plan, setup_s, _ = get_plan(args, None, 0)  # the library's host build of the factors (not timed)
+    F = oracle_factors(plan)
+    n, m = plan.n, plan.m
+    c = W.sphere_coefficients(m)[:, 0]
+    w = np.full(n, 4 * np.pi / n)
     steps = max(1, args.steps)
-    for _ in range(max(0, args.warmup)):
-        pass  # the oracle has no warm state; warm-up steps are not needed
-    value, cb, times = cpu_baseline(args.workload, budget_s=min(120.0, 4.0 * steps), steps=steps)
+    value, cb, times = cpu_baseline(F, c, w, steps, warmup=args.warmup)
     ms = 1000.0 / value
     cb["value"] = value
     cb["unit"] = "transforms/s"
+    desc.update({"nrhs": 1, "plan_setup_s": round(setup_s, 1)})
     line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "transforms/s", "n_gpus": args.gpus, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -482,8 +560,16 @@ def run_ours(args):
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, meta, _ = cpu_baseline(args.workload, budget_s=15.0)
-        cb = dict(meta, value=v, unit="transforms/s")
+        # the oracle's FP64 butterfly apply of this plan on the host cores (a bounded number of
+        # whole transforms), and the exact transform by direct summation on sampled rows
+        F = oracle_factors(plan)
+        c0 = W.sphere_coefficients(m)[:, 0]
+        wv = np.full(n, 4 * np.pi / n)
+        t_one = oracle_step(F, c0, wv)[0]
+        v, meta, _ = cpu_baseline(F, c0, wv, steps=int(max(1, min(8, 12.0 / max(t_one, 1e-3)))), warmup=0)
+        del F
+        cb = dict(meta, value=v, unit="transforms/s",
+                  direct_summation=direct_summation_sample(args.workload, budget_s=10.0))
 
     launches = int(syn_n.sum() + adj_n.sum())  # launches of the K profiled steps = K steps' launches
     desc = workload_desc(args.workload)
@@ -788,9 +874,44 @@ def run_peaks(args):
                       "peaks": out}), flush=True)
 
 
+def replica_command(gpus, argv, port):
+    """The command that starts `gpus` replicas of this script on this node, one rank per GPU."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *argv]
+
+
+def free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def run_ranks(args):
+    """Each rank reports (rank, world size, local rank) and rank 0 prints the gathered layout."""
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    me = [rank, world, int(os.environ.get("LOCAL_RANK", "0"))]
+    if world > 1:
+        dist.init_process_group("gloo")
+        got = [None] * world
+        dist.all_gather_object(got, me)
+        dist.destroy_process_group()
+    else:
+        got = [me]
+    if rank == 0:
+        print(json.dumps({"workload": "ranks", "n_gpus": args.gpus, "ranks": got}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # no launcher: start the replicas here (the same command line on every rank)
+        sys.exit(subprocess.call(replica_command(args.gpus, sys.argv[1:], free_port())))
+    if args.workload == "ranks":
+        run_ranks(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)

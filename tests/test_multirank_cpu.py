@@ -48,3 +48,18 @@ def test_two_gloo_ranks_share_one_plan_and_take_the_max_time(mht_lib, tmp_path):
     assert d[0, 1] == 1 and d[1, 1] == 0          # rank 0 built, rank 1 loaded
     assert d[0, 2] == d[1, 2] and d[0, 3] == d[1, 3]  # the same factors on both ranks
     assert d[2, 0] == 2.0                          # maximum over ranks
+
+
+def test_bench_gpus_n_starts_n_replicas_itself(mht_lib):
+    """`bench.py --gpus 2` without a launcher re-executes itself under torch.distributed.run:
+    two ranks (world size 2, local ranks 0 and 1) report through gloo."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_PORT")}
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--workload", "ranks"],
+                         capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([x for x in out.stdout.splitlines() if x.startswith("{")][-1])
+    assert sorted(tuple(r) for r in line["ranks"]) == [(0, 2, 0), (1, 2, 1)]
