@@ -378,9 +378,9 @@ mht_status mht_plan_set_mode(mht_plan* plan, mht_apply_mode mode);
 
 /* Autotuner: times the candidate launch configurations of every stage of both directions
  * for `nrhs` right-hand sides (SIMT RHS tile 1/2/4/8, bulk-copy ring of 1-8 slots of 16/32/64
- * KB, resident CTAs per SM, and in MHT_APPLY_3XTF32 mode the tensor-core kernel) on the bound
- * workspace, and
- * keeps the fastest per stage; later applies with exactly `nrhs` RHS use them (others use the
+ * KB, resident CTAs per SM, and in the split tensor-core modes the tensor-core kernel) on the
+ * bound workspace, keeps the fastest per stage, and then (up to 8 RHS, automatic path) times
+ * groupings of the small stages at both ends of each direction into one persistent launch; later applies with exactly `nrhs` RHS use them (others use the
  * defaults).  Runs the stages on zeroed workspace buffers only (the caller's vectors are not
  * touched) and synchronizes `stream`; takes about a second on a 15 GB plan.  Results equal
  * the untuned apply's within rounding (RHS tile and kernel change the summation order).
@@ -388,7 +388,11 @@ mht_status mht_plan_set_mode(mht_plan* plan, mht_apply_mode mode);
 mht_status mht_plan_autotune(mht_plan* plan, int64_t nrhs, void* stream);
 /* The tuned configuration of one stage (direction 0 synthesis / 1 analysis; stage 0..L+1):
  * cfg[5] = {tensor cores (0/1), RHS tile, ring slots, CTAs per SM, slot KB} (0 = the default)
- * and its measured milliseconds.  INVALID_ARG if the plan has not been tuned. */
+ * and its measured milliseconds.  stage = -1: the direction's stage grouping, cfg[1] = how many
+ * stages at its start and cfg[2] = how many at its end run as one persistent launch each (with
+ * per-block dependency counters; 0 = none), and the direction's measured milliseconds.  The
+ * autotuner keeps a grouping only when it is at least 2% faster than one launch per stage.
+ * INVALID_ARG if the plan has not been tuned. */
 mht_status mht_plan_tune_info(const mht_plan* plan, int32_t direction, int32_t stage, int32_t* cfg, double* ms);
 
 /* Stage timing for benchmarks.  While enabled, every apply on the plan records a CUDA

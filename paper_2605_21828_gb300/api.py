@@ -111,6 +111,7 @@ class Plan:
     """A built (or imported) butterfly factorization and, once bound, its device copy."""
 
     def __init__(self, handle: C.c_void_p, mode: str, keep=()):
+        self.grouping = {}
         self._h = handle
         self.mode = mode
         self._keep = list(keep)
@@ -279,6 +280,10 @@ class Plan:
                 if L.load().mht_plan_tune_info(self._h, d, st, cfg, C.byref(ms)) == 0:
                     out.append({"direction": d, "stage": st, "tensor": cfg[0], "rhs_tile": cfg[1],
                                 "slots": cfg[2], "ctas_per_sm": cfg[3], "slot_kb": cfg[4], "ms": ms.value})
+        self.grouping = {}
+        for d in (0, 1):  # stages grouped into one persistent launch at each end of a direction
+            if L.load().mht_plan_tune_info(self._h, d, -1, cfg, C.byref(ms)) == 0:
+                self.grouping[d] = {"head": cfg[1], "tail": cfg[2], "ms": ms.value}
         return out
 
     def profile(self, enable: bool = True):

@@ -94,6 +94,7 @@ struct FusedParams {
   unsigned* queue;
   unsigned* status;
   int L, nb, nrhs, slot_bytes, ldx, mrows;
+  int first_stage;            // the launch's first stage: its inputs are complete, no waits
 };
 
 struct ItemInfo {
@@ -293,7 +294,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(FusedParams<R> p) {
       if (g == 0) {
         bool ok = true;
         const int nbs = 1 << (L - min(st, L));
-        if (DIR == 0 && st >= 1 && st <= L) {
+        if (st == p.first_stage) {
+          // a launch over a range of stages: the earlier stages completed in earlier launches
+        } else if (DIR == 0 && st >= 1 && st <= L) {
           const int tau = it.blk / nbs, nu = it.blk % nbs, q = (tau >> 1) * (nbs << 1) + 2 * nu;
           ok = wait_block(p.done, p.targets, st - 1, p.nb, q, p.status) &&
                wait_block(p.done, p.targets, st - 1, p.nb, q + 1, p.status);
@@ -669,29 +672,40 @@ int run_stage(const Ctx& c, int s, int mode, const void* in0, const void* in1, l
 // R^H (l = L..1), V^H.  cfg(dir, s) gives each stage's configuration.
 template <class R, bool C, class Cfg>
 int synth_stages(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool weighted, Cfg&& cfg,
-                 const void* scale = nullptr) {
+                 const void* scale = nullptr, int s_lo = 0, int s_hi = -1) {
   const int L = c.F.L;
+  if (s_hi < 0) s_hi = L + 2;
   const long long nr = c.nrhs;
-  int rc = run_stage<R, C>(c, 0, SYN_ID, cin, nullptr, 1, ldc, lvl(c, 0, 0), nullptr, nr, 1, scale, cfg(0, 0));
-  for (int l = 1; l <= L && !rc; ++l)
+  int rc = 0;
+  if (s_lo == 0 && s_hi > 0)
+    rc = run_stage<R, C>(c, 0, SYN_ID, cin, nullptr, 1, ldc, lvl(c, 0, 0), nullptr, nr, 1, scale, cfg(0, 0));
+  for (int l = std::max(1, s_lo); l <= L && l < s_hi && !rc; ++l)
     rc = run_stage<R, C>(c, l, SYN_ID, lvl(c, 0, l - 1), nullptr, nr, 1, lvl(c, 0, l), nullptr, nr, 1, nullptr,
                          cfg(0, l));
-  if (rc) return rc;
+  if (rc || s_hi <= L + 1) return rc;
   const void* w = weighted ? (const void*)(c.d.base + c.P.weights_off) : nullptr;
   return run_stage<R, C>(c, L + 1, SYN_U, lvl(c, 0, L), nullptr, nr, 1, f, nullptr, 1, ldf, w, cfg(0, L + 1));
 }
 
+// The adjoint's stages k_lo .. k_hi - 1 in dependency order (stage L + 1 - k).
 template <class R, bool C, class Cfg>
-int adjoint_stages(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t ldc, bool weighted, Cfg&& cfg) {
+int adjoint_stages(const Ctx& c, const void* f, int64_t ldf, void* cout, int64_t ldc, bool weighted, Cfg&& cfg,
+                   int k_lo = 0, int k_hi = -1) {
   const int L = c.F.L;
+  if (k_hi < 0) k_hi = L + 2;
   const long long nr = c.nrhs;
   const void* w = weighted ? (const void*)(c.d.base + c.P.weights_off) : nullptr;
+  int rc = 0;
   // U^H: f -> z_L (region A0, level L)
-  int rc = run_stage<R, C>(c, L + 1, ADJ_U, f, nullptr, 1, ldf, lvl(c, 1, L), nullptr, nr, 1, w, cfg(1, L + 1));
-  for (int l = L; l >= 1 && !rc; --l)
+  if (k_lo == 0 && k_hi > 0)
+    rc = run_stage<R, C>(c, L + 1, ADJ_U, f, nullptr, 1, ldf, lvl(c, 1, L), nullptr, nr, 1, w, cfg(1, L + 1));
+  for (int l = L; l >= 1 && !rc; --l) {
+    const int k = L + 1 - l;
+    if (k < k_lo || k >= k_hi) continue;
     rc = run_stage<R, C>(c, l, ADJ_ID, lvl(c, 1, l), l == L ? nullptr : lvl(c, 2, l), nr, 1, lvl(c, 1, l - 1),
                          lvl(c, 2, l - 1), nr, 1, nullptr, cfg(1, l));
-  if (rc) return rc;
+  }
+  if (rc || k_hi <= L + 1) return rc;
   return run_stage<R, C>(c, 0, ADJ_ID, lvl(c, 1, 0), L == 0 ? nullptr : lvl(c, 2, 0), nr, 1, cout, cout, 1, ldc,
                          nullptr, cfg(1, 0));
 }
@@ -721,8 +735,12 @@ unsigned* counters(const Ctx& c, int dir) {
 
 // One launch for every stage of a direction (returns -1 when the shared memory does not fit).
 template <class R, bool C, int RT, int DIR>
-int fused_launch(const Ctx& c, const void* in, long long ld_in, void* out, long long ld_out, bool weighted) {
+int fused_launch(const Ctx& c, const void* in, long long ld_in, void* out, long long ld_out, bool weighted,
+                 int k_lo = 0, int k_hi = -1) {
   const FusedDir& FD = c.P.fused[DIR];
+  const int nst = c.P.L + 2;
+  if (k_hi < 0) k_hi = nst;
+  const int64_t it0 = FD.stage_first[k_lo], nit = FD.stage_first[k_hi] - it0;
   const size_t smem = fused_smem(c.P, DIR, RT);
   if (smem > 227 * 1024) return -1;
   auto kern = k_fused<R, C, RT, DIR>;
@@ -732,7 +750,7 @@ int fused_launch(const Ctx& c, const void* in, long long ld_in, void* out, long 
   const size_t ncnt = size_t(c.P.L + 2) * c.P.nb + 1;
   unsigned* cnt = counters(c, DIR);
   if (int rc = check(cudaMemsetAsync(cnt, 0, ncnt * sizeof(unsigned), c.s), c.err, "counter reset")) return rc;
-  if (FD.nitems == 0) return 0;
+  if (nit == 0) return 0;
   const uint8_t* base = c.d.base;
   FusedParams<R> p;
   p.data = reinterpret_cast<const R*>(base + c.P.data_off);
@@ -741,8 +759,9 @@ int fused_launch(const Ctx& c, const void* in, long long ld_in, void* out, long 
   p.wts = weighted ? reinterpret_cast<const R*>(base + c.P.weights_off) : nullptr;
   p.desc = reinterpret_cast<const MhtBlockDesc*>(base + FD.desc_all_off);
   p.targets = reinterpret_cast<const int*>(base + FD.targets_off);
-  p.items = reinterpret_cast<const MhtPItem*>(base + FD.items_off);
-  p.nitems = int(FD.nitems);
+  p.items = reinterpret_cast<const MhtPItem*>(base + FD.items_off) + it0;
+  p.nitems = int(nit);
+  p.first_stage = DIR == 0 ? k_lo : nst - 1 - k_lo;
   p.vec_off = reinterpret_cast<const long long*>(base + c.P.vecoff_off);
   p.cin = DIR == 0 ? static_cast<const R*>(in) : nullptr;
   p.cout = DIR == 1 ? static_cast<R*>(out) : nullptr;
@@ -762,27 +781,30 @@ int fused_launch(const Ctx& c, const void* in, long long ld_in, void* out, long 
   p.slot_bytes = int(FD.slot_bytes);
   p.ldx = int(std::max<int64_t>(FD.max_ld, 1));
   p.mrows = int(std::max<int64_t>(FD.max_item_rows, 1));
-  const int grid = int(std::min<int64_t>(num_sms(), FD.nitems));
+  const int grid = int(std::min<int64_t>(num_sms(), nit));
   StageTimer timer(c.d.prof, DIR, c.P.L + 2, c.s);
   kern<<<grid, kFusedThreads, smem, c.s>>>(p);
   return check(cudaGetLastError(), c.err, "fused apply launch");
 }
 
 // Smallest RHS tile (1, 2, 4, 8) that covers nrhs in one fused launch, or 0 if none fits.
-int fused_rt(const Ctx& c, int dir) {
-  if (c.d.path != 2 || c.nrhs > 8) return 0;
+int fused_rt_fit(const Ctx& c, int dir) {
+  if (c.nrhs > 8) return 0;
   for (int rt = 1; rt <= 8; rt *= 2)
     if (rt >= c.nrhs) return fused_smem(c.P, dir, rt) <= 227 * 1024 ? rt : 0;
   return 0;
 }
+int fused_rt(const Ctx& c, int dir) { return c.d.path == 2 ? fused_rt_fit(c, dir) : 0; }
 
+// One persistent launch for the stages k_lo .. k_hi - 1 (dependency order) of a direction.
 template <class R, bool C, int DIR>
-int fused_dispatch(const Ctx& c, int rt, const void* in, long long ld_in, void* out, long long ld_out, bool wt) {
+int fused_dispatch(const Ctx& c, int rt, const void* in, long long ld_in, void* out, long long ld_out, bool wt,
+                   int k_lo = 0, int k_hi = -1) {
   switch (rt) {
-    case 1: return fused_launch<R, C, 1, DIR>(c, in, ld_in, out, ld_out, wt);
-    case 2: return fused_launch<R, C, 2, DIR>(c, in, ld_in, out, ld_out, wt);
-    case 4: return fused_launch<R, C, 4, DIR>(c, in, ld_in, out, ld_out, wt);
-    default: return fused_launch<R, C, 8, DIR>(c, in, ld_in, out, ld_out, wt);
+    case 1: return fused_launch<R, C, 1, DIR>(c, in, ld_in, out, ld_out, wt, k_lo, k_hi);
+    case 2: return fused_launch<R, C, 2, DIR>(c, in, ld_in, out, ld_out, wt, k_lo, k_hi);
+    case 4: return fused_launch<R, C, 4, DIR>(c, in, ld_in, out, ld_out, wt, k_lo, k_hi);
+    default: return fused_launch<R, C, 8, DIR>(c, in, ld_in, out, ld_out, wt, k_lo, k_hi);
   }
 }
 
@@ -843,6 +865,35 @@ StageCfg stage_cfg(const Ctx& c, int dir, int s, int default_rt) {
   return g;
 }
 
+// A direction with its first h and last t stages (dependency order) each in one persistent launch
+// with per-block dependency counters, the stages between them one launch each (h = t = 0: every
+// stage its own launch).  The small stages at both ends then overlap instead of each paying a
+// launch, a ramp and a tail.  Returns -1 when the persistent kernel does not fit.
+template <class R, bool C, int DIR>
+int run_direction(const Ctx& c, const void* in, int64_t ld_in, void* out, int64_t ld_out, bool wt, int h, int t) {
+  const int nst = c.P.L + 2;
+  const int rt = pick_rt(c, DIR);
+  auto cfg = [&](int dir, int s) { return stage_cfg(c, dir, s, rt); };
+  const int frt = (h > 0 || t > 0) ? fused_rt_fit(c, DIR) : 0;
+  if ((h > 0 || t > 0) && !frt) return -1;
+  int rc = h > 0 ? fused_dispatch<R, C, DIR>(c, frt, in, ld_in, out, ld_out, wt, 0, h) : 0;
+  if (rc) return rc;
+  if (h + t < nst)
+    rc = DIR == 0 ? synth_stages<R, C>(c, in, ld_in, out, ld_out, wt, cfg, nullptr, h, nst - t)
+                  : adjoint_stages<R, C>(c, in, ld_in, out, ld_out, wt, cfg, h, nst - t);
+  if (rc) return rc;
+  return t > 0 ? fused_dispatch<R, C, DIR>(c, frt, in, ld_in, out, ld_out, wt, std::max(h, nst - t), nst) : 0;
+}
+
+// The stage grouping tuned for this RHS count (both ends, per direction), if any.
+bool tuned_grouping(const Ctx& c, int dir, int& h, int& t) {
+  h = t = 0;
+  if (c.d.tune_nrhs != c.nrhs || c.d.tune_mode != c.mode || use_tc(c) || c.d.path != 0) return false;
+  h = c.d.fuse_head[dir];
+  t = c.d.fuse_tail[dir];
+  return h > 0 || t > 0;
+}
+
 template <class R, bool C>
 int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t ldf, bool wt,
                    const void* scale = nullptr) {
@@ -860,6 +911,11 @@ int synth_dispatch(const Ctx& c, const void* cin, int64_t ldc, void* f, int64_t 
     c.err = "the fused apply does not fit this plan / RHS count";
     return MHT_ERR_UNSUPPORTED;
   }
+  int h, t;
+  if (tuned_grouping(c, 0, h, t)) {
+    const int rc = run_direction<R, C, 0>(c, cin, ldc, f, ldf, wt, h, t);
+    if (rc >= 0) return rc;
+  }
   const int rt = pick_rt(c, 0);
   return synth_stages<R, C>(c, cin, ldc, f, ldf, wt, [&](int dir, int s) { return stage_cfg(c, dir, s, rt); });
 }
@@ -873,6 +929,11 @@ int adjoint_dispatch(const Ctx& c, const void* f, int64_t ldf, void* cout, int64
   if (c.d.path == 2) {
     c.err = "the fused apply does not fit this plan / RHS count";
     return MHT_ERR_UNSUPPORTED;
+  }
+  int h, t;
+  if (tuned_grouping(c, 1, h, t)) {
+    const int rc = run_direction<R, C, 1>(c, f, ldf, cout, ldc, wt, h, t);
+    if (rc >= 0) return rc;
   }
   const int rt = pick_rt(c, 1);
   return adjoint_stages<R, C>(c, f, ldf, cout, ldc, wt, [&](int dir, int s) { return stage_cfg(c, dir, s, rt); });
@@ -978,9 +1039,9 @@ int autotune(Ctx& c, DeviceView& dv, std::vector<TuneRecord>* report) {
       if (report) report->push_back({dir, s, best_cfg, double(best)});
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (rc) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     dv.tune[0].clear();
     dv.tune[1].clear();
     dv.tune_nrhs = 0;
@@ -988,6 +1049,52 @@ int autotune(Ctx& c, DeviceView& dv, std::vector<TuneRecord>* report) {
   }
   dv.tune_nrhs = nr;
   dv.tune_mode = c.mode;
+  // stage grouping at both ends of each direction (one persistent launch for the first h and
+  // one for the last t stages), timed on whole directions with the tuned per-stage shapes
+  dv.fuse_head[0] = dv.fuse_head[1] = dv.fuse_tail[0] = dv.fuse_tail[1] = 0;
+  if (!use_tc(c) && c.d.path == 0 && fused_rt_fit(c, 0) && fused_rt_fit(c, 1)) {
+    const int nst = L + 2;
+    for (int dir = 0; dir < 2 && !rc; ++dir) {
+      float best = 1e30f;
+      int bh = 0, bt = 0;
+      for (int h : {0, 2, 3, 4, 5})
+        for (int t : {0, 2, 3, 4}) {
+          if (h + t > nst || (h > 0 && h >= nst) || (t > 0 && t >= nst)) continue;
+          auto one = [&]() -> int {
+            return dir == 0 ? run_direction<R, C, 0>(c, cbuf, c.F.m, fbuf, c.F.n, false, h, t)
+                            : run_direction<R, C, 1>(c, fbuf, c.F.n, cbuf, c.F.m, false, h, t);
+          };
+          if (one() != 0) {  // does not fit or cannot launch: skipped
+            cudaGetLastError();
+            continue;
+          }
+          if ((rc = check(cudaEventRecord(e0, c.s), c.err, "event"))) break;
+          for (int r = 0; r < 3 && !rc; ++r) rc = one();
+          if (!rc) rc = check(cudaEventRecord(e1, c.s), c.err, "event");
+          if (!rc) rc = check(cudaEventSynchronize(e1), c.err, "event sync");
+          if (rc) break;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if ((h == 0 && t == 0) || ms < best * 0.98f) {  // a grouping must win by 2%
+            best = ms;
+            bh = h;
+            bt = t;
+          }
+        }
+      dv.fuse_head[dir] = bh;
+      dv.fuse_tail[dir] = bt;
+      if (report) report->push_back({dir, -1, StageCfg{0, bh, bt, 0, 0}, double(best)});
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    dv.tune[0].clear();
+    dv.tune[1].clear();
+    dv.tune_nrhs = 0;
+    dv.fuse_head[0] = dv.fuse_head[1] = dv.fuse_tail[0] = dv.fuse_tail[1] = 0;
+    return rc;
+  }
   return check(cudaStreamSynchronize(c.s), c.err, "tune sync");
 }
 

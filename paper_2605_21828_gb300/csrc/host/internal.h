@@ -114,6 +114,7 @@ struct FusedDir {
   size_t slot_bytes = 0;        // bytes of one ring slot (>= the widest row)
   int64_t max_ld = 0;
   int64_t max_item_rows = 0;    // largest persistent item (rows)
+  std::vector<int64_t> stage_first;  // [L+3] first item of the k-th stage in dependency order
 };
 
 struct Packed {
@@ -170,6 +171,9 @@ struct DeviceView {
   int64_t tune_nrhs = 0;          // RHS count the stage configurations were tuned for (0: none)
   mht_apply_mode tune_mode = MHT_APPLY_FP32;
   std::vector<StageCfg> tune[2];  // per direction and stage
+  // stages at the start / end of each direction that run as one persistent launch with
+  // per-block dependency counters (0: none), chosen by the autotuner for tune_nrhs
+  int fuse_head[2] = {0, 0}, fuse_tail[2] = {0, 0};
   struct FilterGraph* filter = nullptr;  // cached CUDA graph of the last spectral filter call
 };
 void filter_graph_destroy(FilterGraph* g);

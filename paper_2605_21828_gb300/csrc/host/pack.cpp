@@ -216,7 +216,9 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
     targets[dir].assign(size_t(nst) * nb, 0);
     FusedDir& FD = P.fused[dir];
     FD.slot_bytes = kSlotBytes;
+    FD.stage_first.assign(nst + 1, 0);
     for (int k = 0; k < nst; ++k) {
+      FD.stage_first[k] = int64_t(pitems[dir].size());
       const int s = dir == 0 ? k : nst - 1 - k;
       for (int64_t b = 0; b < nb; ++b) {
         const MhtBlockDesc& d = desc[dir][s][b];
@@ -238,6 +240,7 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
       }
     }
     FD.nitems = int64_t(pitems[dir].size());
+    FD.stage_first[nst] = FD.nitems;
     for (const MhtPItem& it : pitems[dir]) FD.max_item_rows = std::max<int64_t>(FD.max_item_rows, it.count);
   }
 
