@@ -728,9 +728,10 @@ def run_batch(args):
     achieved = flops / 1e12 / (ms / 1e3)
     factor_bytes = sum(2 * sum(p.level_info(s)["algorithmic_bytes"] for s in range(p.levels + 2)) for p in plans)
 
-    # the tensor-core form: every instance's own apply (3xTF32 block products from 16 RHS on) on
-    # forked streams, replayed from one CUDA graph; its difference from the FP32 results
-    bt.set_mode("3xtf32")
+    # the tensor-core form: every instance's own apply (6xBF16 block products from 16 real / 8
+    # complex RHS on) on forked streams, replayed from one CUDA graph; its difference from the
+    # FP32 results
+    bt.set_mode("6xbf16")
     for i in range(len(plans)):
         bt.c[i].copy_(cin[i])
     for _ in range(Wm):
@@ -771,8 +772,8 @@ def run_batch(args):
             "tensor_core_form": {"ms_per_step": ms_tc, "transforms_per_s": total_rhs / (ms_tc / 1e3),
                                  "speedup_vs_per_instance_fp32": ms_plain / ms_tc,
                                  "max_rel_diff_synthesis_vs_fp32_form": diff, "device_status": status_tc,
-                                 "kernels": "k_tc3 (instances with >= 16 real / 8 complex RHS) and k_rowdot, "
-                                            "8 forked streams in one CUDA graph"},
+                                 "kernels": "k_tcs 6xBF16 (instances with >= 16 real / 8 complex RHS) and "
+                                            "k_rowdot, 8 forked streams in one CUDA graph"},
             "roofline": {"bound": "alu", "kernel": "k_batch (both directions, all instances)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
