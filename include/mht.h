@@ -346,6 +346,11 @@ mht_status mht_noalloc_check(void* stream, int32_t* flags);
  * hold == 0 restores the value from the plan.  Synchronous on `stream`. */
 mht_status mht_noalloc_debug_hold(const mht_plan* plan, void* factor_dev, int32_t hold, void* stream);
 
+/* Testing aid for the out-of-memory path: while `bytes` is non-zero, packing a plan image larger
+ * than `bytes` (build, import, load, clone) fails as a host allocation failure does, with
+ * MHT_ERR_OOM and no plan created.  0 removes the limit.  Process-wide. */
+mht_status mht_debug_host_alloc_limit(size_t bytes);
+
 /* Reads and clears the device status word of the bound workspace (synchronizes `stream`).
  * Every device wait of the apply kernels is bounded (2 s); one that gives up sets a bit and
  * the outputs of that apply are unspecified.  ANY nonzero value means that; the bits say

@@ -94,6 +94,7 @@ SIGNATURES = {
     "mht_plan_check": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "mht_synthesize_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mht_noalloc_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "mht_debug_host_alloc_limit": (C.c_int, [C.c_size_t]),
     "mht_noalloc_debug_hold": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "mht_plan_set_path": (C.c_int, [C.c_void_p, C.c_int32]),
     "mht_plan_set_mode": (C.c_int, [C.c_void_p, C.c_int]),

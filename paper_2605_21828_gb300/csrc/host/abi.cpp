@@ -2,6 +2,7 @@
 #include <omp.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -9,6 +10,14 @@
 #include <string>
 
 #include "internal.h"
+
+namespace mht {
+namespace {
+std::atomic<size_t> g_alloc_limit{0};
+}
+size_t host_alloc_limit() { return g_alloc_limit.load(); }
+void set_host_alloc_limit(size_t bytes) { g_alloc_limit.store(bytes); }
+}  // namespace mht
 
 namespace {
 
@@ -431,6 +440,11 @@ mht_status mht_synthesize_noalloc(const mht_plan* plan, const void* factor_dev, 
     int rc = mht::apply_synthesize_noalloc(plan->P, factor_dev, c_dev, f_dev, stream, err);
     return rc ? set_error(mht_status(rc), err) : MHT_OK;
   });
+}
+
+mht_status mht_debug_host_alloc_limit(size_t bytes) {
+  mht::set_host_alloc_limit(bytes);
+  return MHT_OK;
 }
 
 mht_status mht_noalloc_check(void* stream, int32_t* flags) {

@@ -139,6 +139,10 @@ struct Packed {
   size_t workspace_bytes(int64_t nrhs, int64_t n, int64_t m) const;
 };
 void pack(const Factorization& F, bool fp64, Packed& P);
+// Testing aid: packed images larger than this many bytes fail as a host allocation failure
+// would (0: no limit).
+size_t host_alloc_limit();
+void set_host_alloc_limit(size_t bytes);
 // Checks every descriptor, index, permutation entry and work item of a packed image against
 // the buffers the kernels address with them (throws MHT_ERR_FORMAT).
 void validate_packed(const Packed& P, int64_t n, int64_t m);

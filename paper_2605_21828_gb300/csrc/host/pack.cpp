@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <new>
 
 #include "internal.h"
 
@@ -275,6 +276,7 @@ void pack(const Factorization& F, bool fp64, Packed& P) {
   P.tmap_off = pos;
   P.tmap_bytes = fp64 ? 0 : size_t(2) * nst * nb * 128;
   pos = align_up(pos + P.tmap_bytes, 256);
+  if (const size_t cap = host_alloc_limit(); cap && pos > cap) throw std::bad_alloc();  // testing aid
   P.image.assign(pos, 0);
   uint8_t* img = P.image.data();
 

@@ -469,3 +469,20 @@ def test_noalloc_synthesis_rejects_what_its_fixed_scratch_cannot_serve(mht_lib):
     assert lib.mht_synthesize_noalloc(small._h, C.c_void_p(260), fake, fake, None) == 1
     assert lib.mht_synthesize_noalloc(small._h, fake, None, fake, None) == 1
     assert lib.mht_noalloc_check(None, None) == 1
+
+
+def test_host_allocation_failure_is_reported_as_oom(mht_lib):
+    """An injected host allocation failure (the packed image over a test limit) surfaces as
+    MHT_ERR_OOM from mht_plan_import, creates no plan, and the next import succeeds."""
+    from paper_2605_21828_gb300 import MhtError, Plan, _lib
+    lib = _lib.load()
+    F = _full_rank_factors(4)
+    assert lib.mht_debug_host_alloc_limit(1024) == 0
+    try:
+        with pytest.raises(MhtError, match="OOM"):
+            Plan.from_factors(F, mode="fp32")
+        assert "allocation" in lib.mht_last_error().decode()
+    finally:
+        lib.mht_debug_host_alloc_limit(0)
+    p = Plan.from_factors(F, mode="fp32")
+    assert p.info()["n"] == 16
