@@ -27,10 +27,10 @@
 //   warp 2      gathers the chunk's input entries (the level vector rows named by the block's
 //               index list, the index loaded a chunk ahead) with cp.async into raw B slots;
 //   warps 3-18  split the raw A and B tiles into the pieces' canonical K-major core-matrix
-//               layout (2 stages), then drain the accumulator of the chunk two back (tcgen05.ld;
-//               warp w owns TMEM lanes 32 (w % 4) .. and a quarter of the columns) into FP32
-//               registers with Kahan compensation, and write each unit's rows in the epilogue
-//               (identity term of the ID, weights, scatter).
+//               layout (a ring of stages), then drain the accumulator of the chunk kDrainLag
+//               back (tcgen05.ld; warp w owns TMEM lanes 32 (w % 4) .. and a quarter of the
+//               columns) into FP32 registers with Kahan compensation, and write each unit's
+//               rows in the epilogue (identity term of the ID, weights, scatter).
 // Tensor-core accumulation never spans more than one chunk of 32 columns.  Every mbarrier wait
 // is bounded in time; on timeout the kernel sets status bit 32 and an abort flag, every role
 // leaves its loop, copies and MMAs still in flight are waited for, and the tensor memory is
@@ -54,6 +54,7 @@ constexpr int kMathWarp0 = 3;      // warps 3 .. 18 split, drain and write
 constexpr int kMathWarps = 16;     // four groups of four consecutive warps: lane quadrant x column group
 constexpr int kTcThreads = 32 * (kMathWarp0 + kMathWarps);
 constexpr int kTmemBufs = 4;       // accumulator buffers (N columns each) in flight
+constexpr int kDrainLag = 2;       // chunks between a chunk's split and its drain (< kTmemBufs)
 constexpr int kTcM = 128;          // tile rows = tensor-memory lanes
 constexpr int kTcK = 32;           // FP32 columns of K per chunk
 constexpr int kRawA = kTcM * kTcK * 4;  // one TMA box
@@ -91,14 +92,14 @@ __device__ __forceinline__ unsigned long long gtimer() {
 __device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
 }
-// The waiting thread may sleep (up to the hint, 0.1 ms) until the phase completes, instead of
-// spinning through issue slots the working warps need.
+// The waiting thread may be suspended for a system-dependent time before the test returns
+// false.  (A suspend-time hint, which lets it sleep longer, measured 1.5 % slower.)
 __device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned ph) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(sa(b)), "r"(ph), "r"(100000u)
+      : "r"(sa(b)), "r"(ph)
       : "memory");
   return ok != 0;
 }
@@ -611,8 +612,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
     float2 acc[H / 2], cmn[H / 2];
 #pragma unroll
     for (int j = 0; j < H / 2; ++j) acc[j] = cmn[j] = make_float2(0.f, 0.f);
-    // chunks converted but not yet drained (at most two): unit index << 1 | last chunk of its unit
-    int pq0 = 0, pq1 = 0, np = 0;
+    // chunks converted but not yet drained (at most kDrainLag), as packed epilogue entries
+    int pq[kDrainLag], np = 0;  // oldest first
+    auto pop = [&]() {
+#pragma unroll
+      for (int i = 0; i + 1 < kDrainLag; ++i) pq[i] = pq[i + 1];
+      --np;
+    };
     bool ok = true;
     int g = 0, gdr = 0;  // chunks converted, chunks drained
 
@@ -745,12 +751,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       drain_finish(d, entry);
       return true;
     };
-    // waits for chunk gg's raw tiles (and, with two stages, for the stage to be free)
+    // waits for chunk gg's raw tiles (and, with fewer stages than the drain lag, for the stage
+    // to be free)
     auto convert_wait = [&](int gg) -> bool {
-      // the stage's previous chunk (gg - NS) must have been consumed by its MMAs.  With three
-      // stages this is already known: the drain two chunks behind the split has seen the sums
-      // of every chunk up to gg - 3 complete
-      if (NS < 3 && !wwait(&mma_done[gg % NS], unsigned((gg / NS) & 1) ^ 1u)) return false;
+      // the stage's previous chunk (gg - NS) must have been consumed by its MMAs.  With at least
+      // kDrainLag stages this is already known: every chunk up to gg - kDrainLag has been
+      // drained (its sums, and so all earlier MMAs, complete) before chunk gg is split
+      if (NS < kDrainLag && !wwait(&mma_done[gg % NS], unsigned((gg / NS) & 1) ^ 1u)) return false;
       return wwait(&a_full[gg % RA], unsigned((gg / RA) & 1)) && wwait(&b_full[gg % RB], unsigned((gg / RB) & 1));
     };
     // splits chunk gg (its raw tiles have arrived) into stage gg % NS
@@ -760,8 +767,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       // A: raw 128 x 32 FP32 tile, 128-byte rows, 16-byte chunk j of row r at position j ^ (r & 7)
       const unsigned char* ra = rawA + size_t(sa_) * kRawA;
 #pragma unroll
-      for (int h2 = 0; h2 < 16 / kMathWarps; ++h2) {  // lane -> (row, 8-column group)
-        const int r = (mw + kMathWarps * h2) * 8 + (lane >> 2), k8 = lane & 3;
+      // lane -> (row, 8-column group): the eight lanes of a quarter warp take the eight rows of
+      // one core matrix, so that both the swizzled reads and the 16-byte piece stores of a
+      // quarter warp fall on distinct banks
+      for (int h2 = 0; h2 < 16 / kMathWarps; ++h2) {
+        const int r = (mw + kMathWarps * h2) * 8 + (lane & 7), k8 = lane >> 3;
         const float4 v0 = *reinterpret_cast<const float4*>(ra + r * 128 + (((2 * k8) ^ (r & 7)) << 4));
         const float4 v1 = *reinterpret_cast<const float4*>(ra + r * 128 + (((2 * k8 + 1) ^ (r & 7)) << 4));
         const float xv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
@@ -832,9 +842,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       }
       if (x.nch == 0) {  // no stored columns: drain what is pending, then the rows' identity terms
         while (ok && np > 0) {
-          ok = drain_one(pq0);
-          pq0 = pq1;
-          --np;
+          ok = drain_one(pq[0]);
+          pop();
         }
         if (!ok) break;
         int ld0;
@@ -845,30 +854,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tcs(TcParams p) {
       int ld0 = -1, ue = 0;  // the unit's epilogue record: index load, then packed entry
       epi_issue(x, ld0);
       for (int c = 0; c < x.nch; ++c, ++g) {
-        // the chunk two back drains before this chunk's split: its TMEM read is in flight while
-        // this chunk's tiles are waited for; the previous chunk's MMAs run meanwhile
-        if (np == 2) {
+        // the chunk kDrainLag back drains before this chunk's split: its TMEM read is in flight
+        // while this chunk's tiles are waited for; the later chunks' MMAs run meanwhile
+        if (np == kDrainLag) {
           float d[H];
           if (!(ok = drain_start(d))) break;
           if (!(ok = convert_wait(g))) break;
-          drain_finish(d, pq0);
-          pq0 = pq1;
-          np = 1;
+          drain_finish(d, pq[0]);
+          pop();
         } else if (!(ok = convert_wait(g))) {
           break;
         }
         convert(g);
         if (c == 0) ue = epi_store(x, ld0, us++ & 1);  // after the drains of the previous unit
         const int e = ue | (c == x.nch - 1 ? 1 : 0);
-        if (np == 0) pq0 = e;
-        else pq1 = e;
+#pragma unroll
+        for (int i = 0; i < kDrainLag; ++i)
+          if (i == np) pq[i] = e;
         ++np;
       }
     }
     while (ok && np > 0) {
-      ok = drain_one(pq0);
-      pq0 = pq1;
-      --np;
+      ok = drain_one(pq[0]);
+      pop();
     }
   }
 
