@@ -72,14 +72,26 @@ typedef enum {
 } mht_apply_mode;
 
 typedef enum {
-  MHT_TREE_AUTO = 0,        /* RECT for MHT_EVAL_TORUS, FIEDLER otherwise              */
+  MHT_TREE_AUTO = 0,        /* RECT for MHT_EVAL_TORUS, FIEDLER_MESH when problem->tris
+                               is given, FIEDLER otherwise                            */
   MHT_TREE_FIEDLER = 1,     /* Algorithm 2, mesh-free rule: sign of phi_2 of a kNN
                                heat-kernel graph Laplacian on each node's points      */
   MHT_TREE_RECT = 2,        /* flat periodic square: exact Neumann Fiedler function of
                                each node's rectangle (midpoint cut of the longer side;
                                sin(x1) at the periodic root)                          */
   MHT_TREE_PCA_MEDIAN = 3,  /* median split along the principal axis (equal sizes)     */
-  MHT_TREE_GIVEN = 4        /* problem->space_perm / space_offsets are used as is      */
+  MHT_TREE_GIVEN = 4,       /* problem->space_perm / space_offsets are used as is      */
+  MHT_TREE_FIEDLER_MESH = 5 /* Algorithm 2, patch rule (Sec. 3, Eq. neumann-eigenproblem):
+                               the points are the vertices of the triangle mesh
+                               problem->tris; each node holds a set of triangles (the
+                               patches P) and of points; phi_2 = second eigenfunction of
+                               K phi = lambda M phi on the node's sub-mesh (P1 cotangent
+                               stiffness K, lumped mass M: the homogeneous Neumann
+                               condition is the natural one); M_1 = {P : integral of
+                               phi_2 over P <= 0} (exact for P1: area / 3 x the sum of
+                               the vertex values); a point goes to M_1's side when it is
+                               a vertex of a triangle of M_1 (the closed patch set),
+                               else to M_2's                                           */
 } mht_tree_kind;
 
 typedef enum {
@@ -125,6 +137,9 @@ typedef struct {
   const int64_t* space_perm;    /* MHT_TREE_GIVEN: [n] tree order -> original point    */
   const int64_t* space_offsets; /* MHT_TREE_GIVEN: [2^L + 1] leaf ranges, depth L      */
   const double* weights;        /* [n] quadrature / mass weights w for analysis; NULL = 1 */
+  const int64_t* tris;          /* [ntris * 3] vertex indices (into points, dim 3) of a
+                                   triangle mesh for MHT_TREE_FIEDLER_MESH; or NULL      */
+  int64_t ntris;
 } mht_problem;
 
 typedef struct {

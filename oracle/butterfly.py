@@ -107,6 +107,51 @@ def _split_fiedler(X: np.ndarray):
     return _knn_graph_fiedler(X) <= 0.0
 
 
+def _neumann_phi2(K: sp.spmatrix, Mdiag: np.ndarray) -> np.ndarray:
+    """phi_2 of K phi = lambda M phi (Eq. neumann-eigenproblem discretized by P1 elements; the
+    homogeneous Neumann condition is the natural one, so no boundary rows change).  Dense
+    LAPACK for small sub-meshes, else shift-invert Lanczos just below 0 (K is singular)."""
+    nv = K.shape[0]
+    if nv <= 1500:
+        lam, Phi = sla.eigh(K.toarray(), np.diag(Mdiag), subset_by_index=[0, 1])
+        return Phi[:, 1]
+    shift = -1e-8 * float(np.max(K.diagonal() / Mdiag))
+    lam, Phi = spla.eigsh(K.tocsc(), k=2, M=sp.diags(Mdiag).tocsc(), sigma=shift, which="LM",
+                          v0=np.random.default_rng(0).standard_normal(nv), tol=1e-10)
+    return Phi[:, np.argsort(lam)[1]]
+
+
+def _split_patches(V: np.ndarray, F: np.ndarray, tri_ids: np.ndarray, pts: np.ndarray):
+    """Algorithm 2, patch rule (Sec. 3): the node's sub-mesh is its triangles F[tri_ids];
+    phi_2 is its second Neumann eigenfunction (P1 cotangent stiffness, lumped mass);
+    M_1 = {P : integral of phi_2 over P <= 0}, the P1 integral being area(P)/3 times the sum of
+    the vertex values; a point (a mesh vertex) belongs to M_1 when it is a vertex of a triangle
+    of M_1 (M_1 as a closed set of patches), else to M_2.
+
+    Returns (mask over tri_ids, mask over pts).  Degenerate cases (no triangles, or every point
+    on one side) split the points by order, first half to M_1.
+    """
+    from oracle import fem
+    tri_ids = np.asarray(tri_ids, dtype=np.int64)
+    pts = np.asarray(pts, dtype=np.int64)
+    by_order = np.arange(len(pts)) < len(pts) // 2
+    if len(tri_ids) == 0 or len(pts) == 0:
+        return np.ones(len(tri_ids), dtype=bool), by_order
+    verts, loc = np.unique(F[tri_ids], return_inverse=True)
+    loc = loc.reshape(-1, 3)
+    Vl = V[verts]
+    phi2 = _neumann_phi2(fem.cotan_stiffness(Vl, loc), fem.lumped_mass(Vl, loc))
+    integral = fem.triangle_areas(Vl, loc) / 3.0 * phi2[loc].sum(axis=1)
+    tri_m1 = integral <= 0.0
+    vert_m1 = np.zeros(len(verts), dtype=bool)
+    vert_m1[loc[tri_m1].ravel()] = True
+    pos = np.clip(np.searchsorted(verts, pts), 0, len(verts) - 1)
+    pt_m1 = (verts[pos] == pts) & vert_m1[pos]
+    if pt_m1.all() or not pt_m1.any():
+        pt_m1 = by_order
+    return tri_m1, pt_m1
+
+
 def _split_rect(X: np.ndarray, box):
     """Flat square: exact Neumann Fiedler function of the node's rectangle.
 
@@ -127,18 +172,26 @@ def _split_rect(X: np.ndarray, box):
     return mask, ((a1, b1), (mid, b2)), ((a1, b1), (a2, mid))
 
 
-def space_tree(points: np.ndarray, L: int, kind: str = "fiedler"):
+def space_tree(points: np.ndarray, L: int, kind: str = "fiedler", tris: np.ndarray | None = None):
     """(space_perm, space_off): Fiedler bisection (Algorithm 2) to exactly depth L.
 
-    kind = "fiedler" (kNN graph Laplacian, mesh-free rule) or "rect" (flat periodic square,
-    exact rectangle Fiedler functions).  M_1 becomes the first child.
+    kind = "fiedler" (kNN graph Laplacian, mesh-free rule), "rect" (flat periodic square,
+    exact rectangle Fiedler functions) or "mesh" (patch rule on the triangle mesh ``tris``
+    whose vertices are the points).  M_1 becomes the first child.
     """
     X = np.asarray(points, dtype=np.float64)
-    nodes = [(np.arange(len(X), dtype=np.int64), None)]
+    if kind == "mesh":
+        F = np.asarray(tris, dtype=np.int64).reshape(-1, 3)
+        nodes = [(np.arange(len(X), dtype=np.int64), np.arange(len(F), dtype=np.int64))]
+    else:
+        nodes = [(np.arange(len(X), dtype=np.int64), None)]
     for _ in range(L):
         nxt = []
         for idx, box in nodes:
-            if kind == "rect":
+            if kind == "mesh":
+                tmask, mask = _split_patches(X, F, box, idx)
+                b1, b2 = box[tmask], box[~tmask]
+            elif kind == "rect":
                 mask, b1, b2 = _split_rect(X[idx], box)
             else:
                 mask, b1, b2 = _split_fiedler(X[idx]), None, None

@@ -12,7 +12,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CALLBACK", 4: "NUMERIC", 5: "
           6: "FORMAT", 7: "TIMEOUT", 8: "UNSUPPORTED", 9: "NOT_BOUND"}
 REAL, COMPLEX = 0, 1
 APPLY_FP64, APPLY_FP32, APPLY_3XTF32, APPLY_6XBF16 = 0, 1, 2, 3
-TREE_AUTO, TREE_FIEDLER, TREE_RECT, TREE_PCA_MEDIAN, TREE_GIVEN = 0, 1, 2, 3, 4
+TREE_AUTO, TREE_FIEDLER, TREE_RECT, TREE_PCA_MEDIAN, TREE_GIVEN, TREE_FIEDLER_MESH = 0, 1, 2, 3, 4, 5
 EVAL_CALLBACK, EVAL_TORUS, EVAL_SPHERE, EVAL_DENSE = 0, 1, 2, 3
 
 EVAL_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_int64,
@@ -27,7 +27,8 @@ class Problem(C.Structure):
                 ("torus_modes", C.POINTER(C.c_int64)),
                 ("dense", C.POINTER(C.c_double)), ("ld_dense", C.c_int64),
                 ("space_perm", C.POINTER(C.c_int64)), ("space_offsets", C.POINTER(C.c_int64)),
-                ("weights", C.POINTER(C.c_double))]
+                ("weights", C.POINTER(C.c_double)),
+                ("tris", C.POINTER(C.c_int64)), ("ntris", C.c_int64)]
 
 
 class Options(C.Structure):

@@ -20,7 +20,7 @@ from . import _lib as L
 
 _MODES = {"fp64": L.APPLY_FP64, "fp32": L.APPLY_FP32, "3xtf32": L.APPLY_3XTF32, "6xbf16": L.APPLY_6XBF16}
 _TREES = {"auto": L.TREE_AUTO, "fiedler": L.TREE_FIEDLER, "rect": L.TREE_RECT,
-          "pca": L.TREE_PCA_MEDIAN, "given": L.TREE_GIVEN}
+          "pca": L.TREE_PCA_MEDIAN, "given": L.TREE_GIVEN, "mesh": L.TREE_FIEDLER_MESH}
 _EVALS = {"torus": L.EVAL_TORUS, "sphere": L.EVAL_SPHERE, "dense": L.EVAL_DENSE}
 
 
@@ -123,12 +123,14 @@ class Plan:
     # ---------------------------------------------------------------- construction
     @staticmethod
     def build(*, n, m, eigenvalues, evaluator="sphere", points=None, torus_modes=None,
-              dense=None, callback=None, complex_=None, weights=None, space=None, **opts) -> "Plan":
+              dense=None, callback=None, complex_=None, weights=None, space=None, tris=None,
+              **opts) -> "Plan":
         """Builds the factorization on the host (FP64) through ``mht_build_plan``.
 
         evaluator: "sphere" | "torus" | "dense" | "callback" (then ``callback(rows, cols)``
         returns Phi(rows, cols) as a float64/complex128 array).  ``space`` = (perm, offsets)
-        selects tree="given".
+        selects tree="given".  ``tris`` (ntris x 3 vertex indices; the points are the mesh
+        vertices) makes tree="auto" use Algorithm 2's patch rule ("mesh").
         """
         lib = L.load()
         prob, keep, _ = _problem(n=n, m=m, evaluator=evaluator, points=points, torus_modes=torus_modes,
@@ -140,6 +142,11 @@ class Plan:
             w = np.ascontiguousarray(weights, dtype=np.float64)
             keep.append(w)
             prob.weights = _dptr(w, C.c_double)
+        if tris is not None:
+            tr = np.ascontiguousarray(tris, dtype=np.int64).reshape(-1, 3)
+            keep.append(tr)
+            prob.tris = _dptr(tr, C.c_int64)
+            prob.ntris = len(tr)
         if space is not None:
             sp = np.ascontiguousarray(space[0], dtype=np.int64)
             so = np.ascontiguousarray(space[1], dtype=np.int64)

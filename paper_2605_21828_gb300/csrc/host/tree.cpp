@@ -5,6 +5,7 @@
 // leaves [i 2^(L-d), (i+1) 2^(L-d))).  Space nodes may be empty.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <numeric>
 #include <random>
 
@@ -37,6 +38,7 @@ namespace {
 
 struct Node {
   std::vector<int64_t> idx;
+  std::vector<int64_t> tris;  // FIEDLER_MESH: the node's triangles (patches)
   double box[2][2];  // RECT: [axis][lo, hi]; unused otherwise
   bool periodic_root = false;
 };
@@ -104,6 +106,8 @@ void split_pca(const double* X, int dim, Node& nd, Node& c1, Node& c2) {
 
 void fiedler_split(const double* X, int dim, const std::vector<int64_t>& idx, uint64_t seed,
                    std::vector<char>& in_m1);
+void fiedler_split_mesh(const double* X, const int64_t* tris, const Node& nd, uint64_t seed, Node& c1,
+                        Node& c2);
 
 }  // namespace
 
@@ -118,13 +122,23 @@ void space_tree(const mht_problem& p, mht_tree_kind kind, int L, uint64_t seed,
     return;
   }
   if (kind == MHT_TREE_AUTO)
-    kind = (p.eval_kind == MHT_EVAL_TORUS) ? MHT_TREE_RECT : MHT_TREE_FIEDLER;
+    kind = (p.eval_kind == MHT_EVAL_TORUS) ? MHT_TREE_RECT : (p.tris ? MHT_TREE_FIEDLER_MESH : MHT_TREE_FIEDLER);
   if (!p.points) fail(MHT_ERR_INVALID_ARG, "space tree needs problem->points");
   if (kind == MHT_TREE_RECT && p.dim != 2) fail(MHT_ERR_INVALID_ARG, "MHT_TREE_RECT needs 2-D points");
+  if (kind == MHT_TREE_FIEDLER_MESH) {
+    if (!p.tris || p.ntris <= 0) fail(MHT_ERR_INVALID_ARG, "MHT_TREE_FIEDLER_MESH needs problem->tris");
+    if (p.dim != 3) fail(MHT_ERR_INVALID_ARG, "MHT_TREE_FIEDLER_MESH needs 3-D points (the mesh vertices)");
+    for (int64_t j = 0; j < 3 * p.ntris; ++j)
+      if (p.tris[j] < 0 || p.tris[j] >= n) fail(MHT_ERR_INVALID_ARG, "triangle vertex index out of range");
+  }
   std::vector<Node> cur(1);
   cur[0].idx.resize(n);
   std::iota(cur[0].idx.begin(), cur[0].idx.end(), int64_t(0));
   cur[0].periodic_root = true;
+  if (kind == MHT_TREE_FIEDLER_MESH) {
+    cur[0].tris.resize(p.ntris);
+    std::iota(cur[0].tris.begin(), cur[0].tris.end(), int64_t(0));
+  }
   for (int d = 0; d < L; ++d) {
     std::vector<Node> nxt(cur.size() * 2);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -136,6 +150,9 @@ void space_tree(const mht_problem& p, mht_tree_kind kind, int L, uint64_t seed,
         split_rect(p.points, nd, c1, c2);
       } else if (kind == MHT_TREE_PCA_MEDIAN) {
         split_pca(p.points, p.dim, nd, c1, c2);
+      } else if (kind == MHT_TREE_FIEDLER_MESH) {
+        fiedler_split_mesh(p.points, p.tris, nd, seed + uint64_t(d) * 1000003ull + uint64_t(i), c1, c2);
+        std::vector<int64_t>().swap(nd.tris);
       } else {
         std::vector<char> m1;
         fiedler_split(p.points, p.dim, nd.idx, seed + uint64_t(d) * 1000003ull + uint64_t(i), m1);
@@ -300,6 +317,72 @@ std::vector<double> tridiag_top_vector(const std::vector<double>& a, const std::
   return x;
 }
 
+// Unit vector of the largest eigenvalue of the symmetric operator `op` on the orthogonal
+// complement of the unit vector q (an eigenvector of op): Lanczos from a seeded Gaussian
+// start, deflated against q and fully reorthogonalized (classical Gram-Schmidt twice) at every
+// step, at most mk steps (stops early when the residual norm falls below `tiny`); returns the
+// Ritz vector of the largest Ritz value.  When q's eigenvalue dominates the spectrum (the
+// shifted FEM operator), the rounding-level q component that the Gram-Schmidt pass brings
+// back grows by that ratio every step, so `redeflate` deflates once more after it.
+std::vector<double> lanczos_top(int64_t n, const std::function<void(const std::vector<double>&, std::vector<double>&)>& op,
+                                const std::vector<double>& q, uint64_t seed, int mk_max, double tiny,
+                                bool redeflate = false) {
+  auto deflate = [&](std::vector<double>& x) {
+    double s = 0;
+    for (int64_t j = 0; j < n; ++j) s += q[j] * x[j];
+    for (int64_t j = 0; j < n; ++j) x[j] -= s * q[j];
+  };
+  const int mk = int(std::min<int64_t>(n - 1, mk_max));
+  std::vector<std::vector<double>> V;
+  std::vector<double> al, be;
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> N01;
+  std::vector<double> v(n), w(n);
+  for (auto& x : v) x = N01(rng);
+  deflate(v);
+  double nv = 0;
+  for (double x : v) nv += x * x;
+  nv = std::sqrt(nv);
+  for (auto& x : v) x /= nv;
+  for (int it = 0; it < mk; ++it) {
+    V.push_back(v);
+    op(v, w);
+    double a = 0;
+    for (int64_t j = 0; j < n; ++j) a += w[j] * v[j];
+    al.push_back(a);
+    deflate(w);
+    for (int pass = 0; pass < 2; ++pass) {  // full reorthogonalization, classical GS twice
+      const int nv = int(V.size());
+      std::vector<double> dots(nv, 0.0);
+#pragma omp parallel for schedule(static) if (n * nv > 200000)
+      for (int q = 0; q < nv; ++q) {
+        double s = 0;
+        for (int64_t j = 0; j < n; ++j) s += V[q][j] * w[j];
+        dots[q] = s;
+      }
+#pragma omp parallel for schedule(static) if (n * nv > 200000)
+      for (int64_t j = 0; j < n; ++j) {
+        double s = 0;
+        for (int q = 0; q < nv; ++q) s += dots[q] * V[q][j];
+        w[j] -= s;
+      }
+    }
+    if (redeflate) deflate(w);
+    double bnorm = 0;
+    for (double x : w) bnorm += x * x;
+    bnorm = std::sqrt(bnorm);
+    if (bnorm < tiny || it + 1 == mk) break;
+    be.push_back(bnorm);
+    for (int64_t j = 0; j < n; ++j) v[j] = w[j] / bnorm;
+  }
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  std::vector<double> s = tridiag_top_vector(al, be);
+  std::vector<double> psi(n, 0.0);
+  for (size_t q = 0; q < V.size() && q < s.size(); ++q)
+    for (int64_t j = 0; j < n; ++j) psi[j] += s[q] * V[q][j];
+  return psi;
+}
+
 void fiedler_split(const double* X, int dim, const std::vector<int64_t>& idx, uint64_t seed,
                    std::vector<char>& in_m1) {
   const int64_t n = int64_t(idx.size());
@@ -364,58 +447,7 @@ void fiedler_split(const double* X, int dim, const std::vector<int64_t>& idx, ui
       y[j] = s / (sq[j] * sqn);
     }
   };
-  auto deflate = [&](std::vector<double>& x) {
-    double s = 0;
-    for (int64_t j = 0; j < n; ++j) s += sq[j] * x[j];
-    for (int64_t j = 0; j < n; ++j) x[j] -= s * sq[j];
-  };
-  const int mk = int(std::min<int64_t>(n - 1, 160));
-  std::vector<std::vector<double>> V;
-  std::vector<double> al, be;
-  std::mt19937_64 rng(seed);
-  std::normal_distribution<double> N01;
-  std::vector<double> v(n), w(n);
-  for (auto& x : v) x = N01(rng);
-  deflate(v);
-  double nv = 0;
-  for (double x : v) nv += x * x;
-  nv = std::sqrt(nv);
-  for (auto& x : v) x /= nv;
-  for (int it = 0; it < mk; ++it) {
-    V.push_back(v);
-    applyS(v, w);
-    double a = 0;
-    for (int64_t j = 0; j < n; ++j) a += w[j] * v[j];
-    al.push_back(a);
-    deflate(w);
-    for (int pass = 0; pass < 2; ++pass) {  // full reorthogonalization, classical GS twice
-      const int nv = int(V.size());
-      std::vector<double> dots(nv, 0.0);
-#pragma omp parallel for schedule(static) if (n * nv > 200000)
-      for (int q = 0; q < nv; ++q) {
-        double s = 0;
-        for (int64_t j = 0; j < n; ++j) s += V[q][j] * w[j];
-        dots[q] = s;
-      }
-#pragma omp parallel for schedule(static) if (n * nv > 200000)
-      for (int64_t j = 0; j < n; ++j) {
-        double s = 0;
-        for (int q = 0; q < nv; ++q) s += dots[q] * V[q][j];
-        w[j] -= s;
-      }
-    }
-    double bnorm = 0;
-    for (double x : w) bnorm += x * x;
-    bnorm = std::sqrt(bnorm);
-    if (bnorm < 1e-12 || it + 1 == mk) break;
-    be.push_back(bnorm);
-    for (int64_t j = 0; j < n; ++j) v[j] = w[j] / bnorm;
-  }
-  be.resize(al.size() > 0 ? al.size() - 1 : 0);
-  std::vector<double> s = tridiag_top_vector(al, be);
-  std::vector<double> psi(n, 0.0);
-  for (size_t q = 0; q < V.size() && q < s.size(); ++q)
-    for (int64_t j = 0; j < n; ++j) psi[j] += s[q] * V[q][j];
+  const std::vector<double> psi = lanczos_top(n, applyS, sq, seed, 160, 1e-12);
   int64_t c1 = 0;
   for (int64_t j = 0; j < n; ++j) {
     in_m1[j] = (psi[j] / sq[j] <= 0.0) ? 1 : 0;
@@ -423,6 +455,131 @@ void fiedler_split(const double* X, int dim, const std::vector<int64_t>& idx, ui
   }
   if (c1 == 0 || c1 == n) {  // numerically constant: split by order
     for (int64_t j = 0; j < n; ++j) in_m1[j] = (j < n / 2) ? 1 : 0;
+  }
+}
+
+// ---- patch rule of Algorithm 2 on a triangle mesh (Sec. 3) --------------------------------
+// The node's sub-mesh is the union of its triangles; its vertices are the FEM nodes.  P1
+// cotangent stiffness K (for the corner c of a triangle opposite edge (a, b): K_ab -= cot/2,
+// K_aa, K_bb += cot/2) and barycentric lumped mass m (area / 3 per corner); no boundary term,
+// which is the homogeneous Neumann condition of Eq. neumann-eigenproblem.  phi_2 solves
+// K phi = lambda_2 M phi: psi = M^(1/2) phi is the top eigenvector of sigma I - M^(-1/2) K M^(-1/2)
+// (sigma = its Gershgorin bound) on the complement of M^(1/2) 1 (the null vector).  Triangle P
+// goes to M_1 when area(P) / 3 x (phi_2(a) + phi_2(b) + phi_2(c)) <= 0 (the exact integral of
+// the P1 function); a point goes to M_1's side when it is a vertex of a triangle of M_1.
+void fiedler_split_mesh(const double* X, const int64_t* tris, const Node& nd, uint64_t seed, Node& c1,
+                        Node& c2) {
+  const int64_t nt = int64_t(nd.tris.size());
+  if (nt == 0 || nd.idx.empty()) {  // nothing to cut: points by order, triangles to the first child
+    for (size_t j = 0; j < nd.idx.size(); ++j) (j < nd.idx.size() / 2 ? c1 : c2).idx.push_back(nd.idx[j]);
+    c1.tris = nd.tris;
+    return;
+  }
+  // local vertex numbering of the sub-mesh
+  std::vector<int64_t> verts;
+  verts.reserve(size_t(nt) * 3);
+  for (int64_t t : nd.tris)
+    for (int c = 0; c < 3; ++c) verts.push_back(tris[3 * t + c]);
+  std::sort(verts.begin(), verts.end());
+  verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+  const int64_t nv = int64_t(verts.size());
+  auto local = [&](int64_t g) { return int64_t(std::lower_bound(verts.begin(), verts.end(), g) - verts.begin()); };
+  std::vector<int64_t> lt(size_t(nt) * 3);
+  std::vector<double> area(nt), mass(nv, 0.0);
+  std::vector<std::vector<std::pair<int64_t, double>>> adj(nv);
+  for (int64_t e = 0; e < nt; ++e) {
+    const int64_t t = nd.tris[e];
+    for (int c = 0; c < 3; ++c) lt[3 * e + c] = local(tris[3 * t + c]);
+    const double* P[3] = {X + 3 * tris[3 * t], X + 3 * tris[3 * t + 1], X + 3 * tris[3 * t + 2]};
+    double u[3], v[3], cr[3];
+    for (int d = 0; d < 3; ++d) {
+      u[d] = P[1][d] - P[0][d];
+      v[d] = P[2][d] - P[0][d];
+    }
+    cr[0] = u[1] * v[2] - u[2] * v[1];
+    cr[1] = u[2] * v[0] - u[0] * v[2];
+    cr[2] = u[0] * v[1] - u[1] * v[0];
+    area[e] = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    for (int c = 0; c < 3; ++c) mass[lt[3 * e + c]] += area[e] / 3.0;
+    for (int c = 0; c < 3; ++c) {  // corner c opposite edge (a, b)
+      const int a = (c + 1) % 3, b = (c + 2) % 3;
+      double x[3], y[3], dot = 0;
+      for (int d = 0; d < 3; ++d) {
+        x[d] = P[a][d] - P[c][d];
+        y[d] = P[b][d] - P[c][d];
+        dot += x[d] * y[d];
+      }
+      const double twice_area = 2.0 * area[e];
+      if (!(twice_area > 0)) continue;
+      const double w = 0.5 * dot / twice_area;  // cot(angle at c) / 2
+      const int64_t la = lt[3 * e + a], lb = lt[3 * e + b];
+      adj[la].push_back({lb, -w});
+      adj[lb].push_back({la, -w});
+      adj[la].push_back({la, w});
+      adj[lb].push_back({lb, w});
+    }
+  }
+  // CSR of K with duplicates summed
+  std::vector<int64_t> rp(nv + 1, 0), ci;
+  std::vector<double> cv;
+  for (int64_t i = 0; i < nv; ++i) {
+    auto& a = adj[i];
+    std::sort(a.begin(), a.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (size_t q = 0; q < a.size(); ++q) {
+      if (q > 0 && a[q].first == a[q - 1].first) {
+        cv.back() += a[q].second;
+        continue;
+      }
+      ci.push_back(a[q].first);
+      cv.push_back(a[q].second);
+    }
+    rp[i + 1] = int64_t(ci.size());
+    std::vector<std::pair<int64_t, double>>().swap(a);
+  }
+  std::vector<double> rs(nv), q(nv);  // M^(-1/2), unit M^(1/2) 1
+  double qn = 0;
+  for (int64_t i = 0; i < nv; ++i) {
+    if (!(mass[i] > 0)) mass[i] = 1e-300;
+    rs[i] = 1.0 / std::sqrt(mass[i]);
+    q[i] = std::sqrt(mass[i]);
+    qn += mass[i];
+  }
+  qn = std::sqrt(qn);
+  for (auto& x : q) x /= qn;
+  double sigma = 0;  // Gershgorin bound of S = M^(-1/2) K M^(-1/2)
+  for (int64_t i = 0; i < nv; ++i) {
+    double r = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) r += std::fabs(cv[k]) * rs[i] * rs[ci[k]];
+    sigma = std::max(sigma, r);
+  }
+  if (!(sigma > 0)) sigma = 1.0;
+  auto op = [&](const std::vector<double>& x, std::vector<double>& y) {  // y = sigma x - S x
+#pragma omp parallel for schedule(static) if (nv > 8192)
+    for (int64_t i = 0; i < nv; ++i) {
+      double s = 0;
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += cv[k] * rs[ci[k]] * x[ci[k]];
+      y[i] = sigma * x[i] - rs[i] * s;
+    }
+  };
+  const std::vector<double> psi = lanczos_top(nv, op, q, seed, 240, 1e-12 * sigma, true);
+  std::vector<char> vert_m1(nv, 0);
+  for (int64_t e = 0; e < nt; ++e) {
+    double s = 0;
+    for (int c = 0; c < 3; ++c) s += psi[lt[3 * e + c]] * rs[lt[3 * e + c]];
+    const bool m1 = area[e] / 3.0 * s <= 0.0;
+    (m1 ? c1 : c2).tris.push_back(nd.tris[e]);
+    if (m1)
+      for (int c = 0; c < 3; ++c) vert_m1[lt[3 * e + c]] = 1;
+  }
+  for (int64_t g : nd.idx) {
+    const int64_t i = local(g);
+    const bool in = i < nv && verts[i] == g && vert_m1[i];
+    (in ? c1 : c2).idx.push_back(g);
+  }
+  if (c1.idx.empty() || c2.idx.empty()) {  // numerically constant: points by order
+    c1.idx.clear();
+    c2.idx.clear();
+    for (size_t j = 0; j < nd.idx.size(); ++j) (j < nd.idx.size() / 2 ? c1 : c2).idx.push_back(nd.idx[j]);
   }
 }
 

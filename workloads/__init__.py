@@ -152,6 +152,27 @@ def icosphere(level: int):
     return np.array(V), np.array(F, dtype=np.int64)
 
 
+def criss_cross_rectangle(a: float, b: float, nx: int, ny: int):
+    """Flat rectangle [0, a] x [0, b] (z = 0) meshed by an nx x ny grid of cells, each split
+    into four triangles by its centre vertex: (vertices (V,3), triangles (F,3) int64).  The
+    mesh is symmetric under x -> a - x and y -> b - y.  Grid vertices come first (row-major in
+    y, then x), then the cell centres."""
+    xs, ys = np.linspace(0.0, a, nx + 1), np.linspace(0.0, b, ny + 1)
+    gx, gy = np.meshgrid(xs, ys)
+    grid = np.stack([gx.ravel(), gy.ravel(), np.zeros(gx.size)], axis=1)
+    cx, cy = np.meshgrid(0.5 * (xs[1:] + xs[:-1]), 0.5 * (ys[1:] + ys[:-1]))
+    centres = np.stack([cx.ravel(), cy.ravel(), np.zeros(cx.size)], axis=1)
+    V = np.concatenate([grid, centres])
+    g = lambda i, j: j * (nx + 1) + i  # noqa: E731
+    F = []
+    for j in range(ny):
+        for i in range(nx):
+            c = len(grid) + j * nx + i
+            p00, p10, p11, p01 = g(i, j), g(i + 1, j), g(i + 1, j + 1), g(i, j + 1)
+            F += [(p00, p10, c), (p10, p11, c), (p11, p01, c), (p01, p00, c)]
+    return V, np.array(F, dtype=np.int64)
+
+
 def random_polynomial_height(points: np.ndarray, degree: int = 6, seed: int = 3) -> np.ndarray:
     """h(x) = sum over monomials x^a y^b z^c (a+b+c <= degree) of seeded N(0,1) weights."""
     rng = np.random.default_rng(seed)
