@@ -177,7 +177,8 @@ typedef struct {
   int32_t* local_perm;     /* [sum of K over all blocks]                               */
   double* transfer;        /* [sum of r (K - r)] (x2 if complex)                       */
   double* column_bases;    /* [sum of |tau| r_L] (x2 if complex)                       */
-  double* weights;         /* [n] or NULL (import only)                                */
+  double* weights;         /* [n] or NULL: read by import; written by export when the
+                              plan has analysis weights (left as is otherwise)        */
 } mht_factors;
 
 typedef struct {

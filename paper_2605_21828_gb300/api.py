@@ -231,7 +231,10 @@ class Plan:
         fa.local_perm = _dptr(out["local_perm"], C.c_int32)
         fa.transfer = _dptr(out["transfer"], C.c_double)
         fa.column_bases = _dptr(out["column_bases"], C.c_double)
+        w = np.full(info["n"], np.nan)
+        fa.weights = _dptr(w, C.c_double)
         L.check(L.load().mht_plan_export(self._h, C.byref(fa)))
+        out["weights"] = None if np.isnan(w).all() else w  # the analysis weights, if the plan has them
         out["local_perm"] = out["local_perm"][:info["local_perm_entries"]]
         t = out["transfer"][:info["transfer_entries"] * W]
         u = out["column_bases"][:info["column_basis_entries"] * W]
