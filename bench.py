@@ -46,6 +46,16 @@ WORKLOADS = {
     "sphere16384": (16384, 127, 128, 1e-6),   # small case for profiler captures
     "sphere4096": (4096, 63, 128, 1e-6),
 }
+# the deformed-sphere FEM configuration at its stated size: its plan comes from a file written by
+# tests/c3_plan.py (the eigenpairs take half an hour of host time), named by --plan-cache or
+# the environment variable MHT_C3_PLAN
+C3 = "c3"
+C3_DESC = {"workload": "deformed-sphere mesh: icosphere level 6 (40962 vertices, 81920 triangles), radius "
+                       "1 + 0.2 h / max|h|, P1 cotangent stiffness + lumped mass, the 4096 lowest generalized "
+                       "eigenpairs (FP64 host spectral slicing), eps=1e-6, leaf 128, patch-rule Fiedler tree, "
+                       "FP32 factors, lumped-mass weights",
+           "n": 40962, "m": 4096, "eps": 1e-6, "leaf_size": 128,
+           "l2": "packed factors (0.2 GB) > 129 MB L2 (streamed from HBM every step; no flush needed)"}
 
 
 def parse():
@@ -56,7 +66,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--multi-rhs", type=int, default=64, help="extra measurement at this many RHS (0: off)")
-    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + ["batch64", "torus_sweep", "peaks", "ranks"],
+    ap.add_argument("--workload", default="sphere65536", choices=sorted(WORKLOADS) + [C3, "batch64", "torus_sweep", "peaks", "ranks"],
                     help="batch64: 64 ragged instances (torus / sphere / deformed sphere, n in [2000, 40000], "
                          "m = n/4, 1-128 RHS each) in one persistent launch per direction; torus_sweep: the flat-torus "
                          "memory law (m = ceil(n/25), eps 1e-3 and 1e-6) with single-RHS apply times; peaks: "
@@ -73,6 +83,8 @@ def parse():
 
 
 def workload_desc(name):
+    if name == C3:
+        return dict(C3_DESC)
     n, lmax, leaf, eps = WORKLOADS[name]
     return {"workload": f"unit sphere: n={n} jittered-Fibonacci points, m={(lmax + 1) ** 2} real spherical "
                         f"harmonics (degree <= {lmax}), eps={eps:g}, leaf {leaf}, FP32 factors, weights 4pi/n",
@@ -122,6 +134,15 @@ def blas_threads(k):
                     put(ctypes.c_int(int(k)))
                     return prev
     return None
+
+
+def analysis_weights(plan, workload):
+    """The plan's analysis weights: quadrature 4 pi / n on the sphere; on the mesh the lumped
+    mass stored in the plan file."""
+    import numpy as np
+    if workload == C3:
+        return plan.export()["weights"]
+    return np.full(plan.n, 4 * np.pi / plan.n)
 
 
 def oracle_factors(plan):
@@ -195,7 +216,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload not in WORKLOADS:
+    if args.workload not in WORKLOADS and args.workload != C3:
         raise SystemExit("--impl reference times the oracle on the single-plan workloads only")
     import numpy as np
 
@@ -207,7 +228,7 @@ def run_reference(args):
     F = oracle_factors(plan)
     n, m = plan.n, plan.m
     c = W.sphere_coefficients(m)[:, 0]
-    w = np.full(n, 4 * np.pi / n)
+    w = analysis_weights(plan, args.workload)
     steps = max(1, args.steps)
     value, cb, times = cpu_baseline(F, c, w, steps, warmup=args.warmup)
     ms = 1000.0 / value
@@ -287,10 +308,16 @@ def get_plan(args, dist, rank):
 
     import workloads as W
     from paper_2605_21828_gb300 import Plan
+    t0 = time.time()
+    if args.workload == C3:
+        path = args.plan_cache or os.environ.get("MHT_C3_PLAN", "")
+        if not path or not os.path.exists(path):
+            raise SystemExit("--workload c3 reads a saved plan (--plan-cache or MHT_C3_PLAN; "
+                             "written by python tests/c3_plan.py OUT.plan)")
+        return Plan.load(path, mode="fp32"), time.time() - t0, False
     n, lmax, leaf, eps = WORKLOADS[args.workload]
     m = (lmax + 1) ** 2
     cache = args.plan_cache or os.path.join(tempfile.gettempdir(), f"mht_{args.workload}.plan")
-    t0 = time.time()
     built = False
     if rank == 0 and not os.path.exists(cache):
         X = W.fibonacci_points(n)
@@ -575,12 +602,13 @@ def run_ours(args):
         # whole transforms), and the exact transform by direct summation on sampled rows
         F = oracle_factors(plan)
         c0 = W.sphere_coefficients(m)[:, 0]
-        wv = np.full(n, 4 * np.pi / n)
+        wv = analysis_weights(plan, args.workload)
         t_one = oracle_step(F, c0, wv)[0]
         v, meta, _ = cpu_baseline(F, c0, wv, steps=int(max(1, min(8, 12.0 / max(t_one, 1e-3)))), warmup=0)
         del F
-        cb = dict(meta, value=v, unit="transforms/s",
-                  direct_summation=direct_summation_sample(args.workload, budget_s=10.0))
+        cb = dict(meta, value=v, unit="transforms/s")
+        if args.workload in WORKLOADS:  # the sphere's Phi has a closed form to sum directly
+            cb["direct_summation"] = direct_summation_sample(args.workload, budget_s=10.0)
 
     launches = int(syn_n.sum() + adj_n.sum())  # launches of the K profiled steps = K steps' launches
     desc = workload_desc(args.workload)
